@@ -1,0 +1,363 @@
+"""Throughput benchmark of the thermal lattice Boltzmann step on GB300.
+
+Workload: side-heated cubic cell, 257^3 nodes, Ra = 1e7, Pr = 0.71, hot wall
+x = 0 (T = +1/2), cold wall x = H (T = -1/2), four adiabatic walls, all walls
+no-slip; free-fall scaling with U = 0.1.  One benchmark step is one chunk of
+100 lattice Boltzmann time steps (D3Q19 + D3Q7 stream-and-collide of every
+node) with the global diagnostics (Nu, Re, dissipation) sampled once, i.e. a
+pass over every row of the hot path.  The state (1.77 GB in FP32, 0.88 GB in
+FP16) is far larger than the 129 MB L2, so no flush is needed between steps.
+
+Metric: GLUPS = lattice-node updates of both distributions per second
+(nodes x time steps / s), whole job.  The line also carries the HBM roofline
+fraction of the step kernel, the FP16/BF16-storage variants, the end-to-end
+figure through the C ABI with host buffers, and the FP64 CPU oracle timed on
+this machine's host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_EDGE = 257
+RA, PR, U = 1e7, 0.71, 0.1
+CHUNK = 100                  # LB time steps per benchmark step
+BYTES_PER_NODE = {"fp32": 208, "fp16s": 104, "bf16s": 104}  # 26 populations read + written
+NOMINAL_HBM_GBS = 8000.0
+FALLBACK_HBM_GBS = 6800.0
+METRIC = "GLUPS (D3Q19+D3Q7) and % HBM roofline at 257^3, FP32 vs FP16 storage"
+STEP_KERNEL_SRC = [os.path.join(ROOT, "paper_1903_08882_gb300", "csrc", f)
+                   for f in ("lbm_kernels.cu", "lbm_device.cuh")]
+
+
+def _peak_hbm():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def _kernel_hash():
+    h = hashlib.sha256()
+    for p in STEP_KERNEL_SRC:
+        with open(p, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _profiled_traffic(storage):
+    """DRAM bytes per step-kernel launch from the committed ncu summary, if it
+    was taken on the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "step_kernel_dram_traffic.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
+    if not m or m.group(1) != _kernel_hash():
+        return None
+    m = re.search(rf"traffic_per_launch_{storage}_257:\s*([0-9.eE+]+)", txt)
+    return float(m.group(1)) if m else None
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            parts = [x.strip() for x in l.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if parts[4 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+        return dist, int(os.environ["RANK"]), ws, int(os.environ.get("LOCAL_RANK", "0"))
+    return None, 0, 1, 0
+
+
+def _max_over_ranks(dist, x):
+    if dist is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _barrier(dist):
+    import torch
+
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+        torch.cuda.synchronize()
+
+
+def _cpu_oracle_rate(max_seconds=15.0, min_steps=2):
+    """FP64 oracle (the test reference, as it stands) on a bounded sample of
+    the workload: a 257 x 257 x 8 slab of the side-heated 257^3 cell with the
+    same walls, stepped until about max_seconds have passed."""
+    import oracle
+
+    oracle.build()
+    nz = 8
+    p = oracle.cell((N_EDGE, N_EDGE, nz), RA, PR, oracle.side_heated_walls(), H=N_EDGE)
+    f, g = oracle.init_equilibrium(p, 1.0, np.zeros(3), 0.0)
+    f, g = oracle.run(p, f, g, 1)  # warm the pages
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        f, g = oracle.run(p, f, g, 1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if steps >= min_steps and el >= max_seconds:
+            break
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    nodes = N_EDGE * N_EDGE * nz
+    return nodes * steps / el / 1e9, threads, f"{N_EDGE}x{N_EDGE}x{nz} slab of the 257^3 side-heated cell, " \
+                                               f"{steps} FP64 oracle steps in {el:.1f} s"
+
+
+def run_reference(args):
+    dist, rank, ws, _ = _dist()
+    if rank != 0:
+        return
+    per_step, threads = [], None
+    for k in range(args.warmup + args.steps):
+        rate, threads, sample = _cpu_oracle_rate(max_seconds=2.0, min_steps=1)
+        if k >= args.warmup:
+            per_step.append(rate)
+    value = statistics.mean(per_step)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "side-heated cube 257^3, Ra=1e7, Pr=0.71, U=0.1 (bounded slab sample)"},
+        "cpu_baseline": {"value": value, "unit": "GLUPS", "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def _time_chunks(lat, k, stream):
+    import torch
+
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(k):
+        lat.step(CHUNK)
+    ev1.record(stream)
+    ev1.synchronize()
+    return ev0.elapsed_time(ev1) / 1e3
+
+
+def _step_kernel_seconds(lat, stream, launches=99):
+    """Average duration of the step kernel: `launches` consecutive plain step
+    launches (no diagnostic sample falls among them), bracketed by events on
+    the library's stream."""
+    import torch
+
+    c = lat.diagnostics(raise_on_diverged=False)["step"]
+    lat.step((-c) % CHUNK + 1)  # now one past a sampling step
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    lat.step(launches)
+    ev1.record(stream)
+    ev1.synchronize()
+    return ev0.elapsed_time(ev1) / 1e3 / launches
+
+
+def bench_storage(lbm, storage, args, stream, dist, with_e2e):
+    import torch
+
+    N = N_EDGE
+    nodes = N ** 3
+    lat = lbm.Lattice(N, N, N, lbm.walls_side_heated(), Ra=RA, Pr=PR, U=U, storage=storage,
+                      diag_every=CHUNK, stream=stream)
+    res = {}
+    try:
+        for _ in range(args.warmup):
+            lat.step(CHUNK)
+        _barrier(dist)
+        with ClockSampler(torch.cuda.current_device()) as cs:
+            dt = _time_chunks(lat, args.steps, stream)
+        _barrier(dist)
+        dt = _max_over_ranks(dist, dt)
+        res["seconds"] = dt
+        res["glups"] = nodes * CHUNK * args.steps * (dist.get_world_size() if dist else 1) / dt / 1e9
+        res["clocks"] = cs.summary()
+        tk = _step_kernel_seconds(lat, stream)
+        res["kernel_seconds"] = tk
+        d = lat.diagnostics(raise_on_diverged=False)
+        res["Nu_hot"] = float(d["Nu_face"][0])
+        res["diverged"] = bool(d["diverged"])
+        if with_e2e:
+            res["e2e"] = _e2e(lbm, lat, args, stream, dist)
+    finally:
+        lat.close()
+    return res
+
+
+def _e2e(lbm, lat, args, stream, dist):
+    """Same metric through the public API with host buffers: every step uploads
+    its input fields (rho, u, T) from pinned host memory via lbm_set_fields,
+    advances one chunk and reads the diagnostics back to the host."""
+    import torch
+
+    N = N_EDGE
+    sh = (N, N, N)
+    rho = torch.ones(sh, dtype=torch.float64).pin_memory().numpy()
+    u3 = torch.zeros((3,) + sh, dtype=torch.float64).pin_memory().numpy()
+    T = torch.zeros(sh, dtype=torch.float64).pin_memory().numpy()
+    for _ in range(max(1, args.warmup // 2)):
+        lat.set_fields(rho, u3, T)
+        lat.step(CHUNK)
+        lat.diagnostics(raise_on_diverged=False)
+    _barrier(dist)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        lat.set_fields(rho, u3, T)
+        lat.step(CHUNK)
+        lat.diagnostics(raise_on_diverged=False)
+    torch.cuda.synchronize()
+    dt = _max_over_ranks(dist, time.perf_counter() - t0)
+    ws = dist.get_world_size() if dist else 1
+    return {"value": N ** 3 * CHUNK * args.steps * ws / dt / 1e9, "unit": "GLUPS",
+            "h2d_bytes_per_step": 5 * 4 * N ** 3, "d2h_bytes_per_step": 8 * (2 * 24 + 1)}
+
+
+def run_gpu(args):
+    import torch
+
+    dist, rank, ws, local = _dist()
+    torch.cuda.set_device(local)
+    from paper_1903_08882_gb300 import _build, lbm
+
+    if not _build.up_to_date():
+        _build.build()
+    stream = torch.cuda.Stream()
+    peak, peak_kind = _peak_hbm()
+    storages = ["fp32"] if args.fp32_only else ["fp32", "fp16s", "bf16s"]
+    results = {}
+    with torch.cuda.stream(stream):
+        for st in storages:
+            results[st] = bench_storage(lbm, st, args, stream, dist, with_e2e=(st == "fp32"))
+    if rank != 0:
+        return
+    main = results["fp32"]
+    nodes = N_EDGE ** 3
+
+    def roof(r, st):
+        ach = BYTES_PER_NODE[st] * nodes / r["kernel_seconds"] / 1e9
+        return {"bound": "hbm", "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(ach / peak, 4), "peak_kind": peak_kind,
+                "frac_of_nominal_8000": round(ach / NOMINAL_HBM_GBS, 4),
+                "algorithmic_bytes_per_launch": BYTES_PER_NODE[st] * nodes,
+                "traffic": _profiled_traffic(st), "kernel": f"step kernel (AA pattern, {st} storage)",
+                "kernel_ms": round(r["kernel_seconds"] * 1e3, 4),
+                "kernel_glups": round(nodes / r["kernel_seconds"] / 1e9, 3)}
+
+    cpu_rate, threads, sample = _cpu_oracle_rate() if not args.no_cpu else (None, None, None)
+    line = {
+        "metric": METRIC, "value": round(main["glups"], 3), "unit": "GLUPS", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(main["seconds"] / args.steps * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "side-heated cube 257^3, Ra=1e7, Pr=0.71, U=0.1, FP32 storage, AA streaming",
+                   "lb_steps_per_step": CHUNK, "diag_every": CHUNK, "nodes": nodes,
+                   "l2": "state (1.77 GB FP32) larger than L2, no flush",
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+        "roofline": roof(main, "fp32"),
+        "clocks": main["clocks"],
+        "e2e": main.get("e2e"),
+        "gpu_launches": (CHUNK + 2) * args.steps,
+        "cpu_baseline": ({"value": cpu_rate, "unit": "GLUPS", "cores": threads, "kind": "oracle",
+                          "sample": sample} if cpu_rate else None),
+        "storage_variants": {st: {"value": round(r["glups"], 3), "unit": "GLUPS",
+                                  "ms_per_step": round(r["seconds"] / args.steps * 1e3, 3),
+                                  "roofline": roof(r, st), "clocks": r["clocks"],
+                                  "speedup_vs_fp32": round(r["glups"] / main["glups"], 3)}
+                             for st, r in results.items() if st != "fp32"},
+        "Nu_hot_after_run": main["Nu_hot"],
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp32-only", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,227 @@
+/*
+ * lbm.h - C ABI of the GB300 thermal lattice Boltzmann library.
+ *
+ * The library advances the double-distribution thermal lattice Boltzmann model
+ * of Xu, Shi & Xi (arXiv:1903.08882) on one GPU:
+ *   - a D3Q19 multiple-relaxation-time flow distribution f with Guo forcing
+ *     and Boussinesq buoyancy F = rho g beta (T - T0) z-hat (Sec. 2.2, Eq. MRT);
+ *   - a D3Q7 multiple-relaxation-time temperature distribution g whose rates
+ *     make the fourth-order error isotropic (Sec. 2.3, Eq. MRT_T, Eq. magic,
+ *     Eq. 4th, Eq. qk, Eq. qnu);
+ *   - half-way bounce-back no-slip walls for f (Sec. 2.2), half-way
+ *     anti-bounce-back Dirichlet walls and half-way bounce-back adiabatic walls
+ *     for g (Sec. 2.3).
+ *
+ * Conventions shared by every entry point:
+ *   - Lattice units, delta_x = delta_t = 1.  Node (x, y, z), 0 <= x < nx, sits
+ *     at x + 1/2; the walls of a non-periodic axis lie at 0 and nx (half-way).
+ *   - Faces are indexed 0..5 = -x, +x, -y, +y, -z, +z.  Gravity points along
+ *     -z, so buoyancy pushes warm fluid along +z.
+ *   - Host arrays are component-major with x fastest: a[c][z][y][x].  Velocity
+ *     fields have 3 components (u, v, w); f has 19 and g has 7, in the
+ *     paper's velocity order (e_0..e_18 of Sec. 2.2, e_0..e_6 of Sec. 2.3).
+ *   - Populations exchanged with the host are absolute values in double
+ *     precision.  Inside the library they are stored as deviations from the
+ *     rest state, f_i - w_i rho0 and g_i - w_i T0 (rho0 = 1, T0 = 0), in FP32,
+ *     FP16 or BF16; all arithmetic is FP32 and global sums are FP64.
+ *   - Every function returns an lbm_status; nothing throws.  On failure
+ *     lbm_last_error() holds a message.  Calls on one context must not overlap
+ *     from several host threads.
+ *   - lbm_step and lbm_set_* are asynchronous on the context's stream; the
+ *     functions that return host data synchronise that stream.
+ */
+#ifndef LBM_GB300_H
+#define LBM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_PARAM = 1,    /* invalid argument or parameter set            */
+    LBM_ERR_CUDA = 2,     /* a CUDA runtime call failed                    */
+    LBM_ERR_OOM = 3,      /* device allocation failed                      */
+    LBM_ERR_DIVERGED = 4, /* non-finite value or |u| > c_s in the state    */
+    LBM_ERR_TIMEOUT = 5,  /* a bounded device wait ran out                 */
+    LBM_ERR_STATE = 6     /* call not valid in the context's current state */
+} lbm_status;
+
+typedef enum {
+    LBM_WALL_ADIABATIC = 0, /* no-slip, zero heat flux (half-way bounce-back) */
+    LBM_WALL_DIRICHLET = 1, /* no-slip, T = T_w (half-way anti-bounce-back)   */
+    LBM_WALL_PERIODIC = 2   /* no wall: the axis wraps (both faces of an axis) */
+} lbm_wall_kind;
+
+typedef enum {
+    LBM_FP32 = 0,  /* 4 bytes per population, 104 B per node   */
+    LBM_FP16S = 1, /* IEEE half deviations, 52 B per node       */
+    LBM_BF16S = 2  /* bfloat16 deviations, 52 B per node        */
+} lbm_storage;
+
+typedef enum {
+    LBM_STREAM_AA = 0,   /* in-place AA pattern, one population buffer      */
+    LBM_STREAM_PULL2 = 1 /* two buffers, pull streaming (fallback kernel)   */
+} lbm_streaming;
+
+typedef struct {
+    int kind;   /* lbm_wall_kind */
+    double T_w; /* wall temperature, used when kind == LBM_WALL_DIRICHLET */
+} lbm_wall;
+
+/* Parameters of one cell.
+ * With derive = 1 the transport coefficients follow the free-fall scaling of
+ * Sec. 2.1 with dT = 1: nu = U H sqrt(Pr/Ra), kappa = nu/Pr, g beta = U^2/H
+ * (H <= 0 means H = nz).  With derive = 0, nu, kappa and gbeta are used as
+ * given and Ra, Pr only label the run; U and H still scale the diagnostics.
+ * Validity (else LBM_ERR_PARAM): every n >= 3; tau_f = 3 nu + 1/2 > 1/2;
+ * a_T = 42 sqrt(3) kappa - 6 in (-6, 1) so that both D3Q7 weights are
+ * positive; 0 < U <= 0.2; both faces of an axis periodic or neither. */
+typedef struct {
+    int nx, ny, nz;
+    double Ra, Pr, U, H;
+    int derive;
+    double nu, kappa, gbeta;
+    double body_force[3]; /* constant force density added to the buoyancy force */
+    lbm_wall wall[6];
+    int storage;    /* lbm_storage */
+    int streaming;  /* lbm_streaming */
+    int diag_every; /* lbm_step samples the diagnostics every diag_every steps (0: never) */
+    int block_size; /* threads per block of the step kernels, 0 = library default */
+} lbm_params;
+
+/* Device memory provider.  alloc returns device memory of at least `bytes`
+ * bytes usable on `stream` (NULL on failure); free releases it.  A NULL
+ * allocator makes the library call cudaMalloc / cudaFree itself.  The Python
+ * binding passes PyTorch's caching allocator here. */
+typedef struct {
+    void *(*alloc)(size_t bytes, void *stream, void *user);
+    void (*free)(void *ptr, size_t bytes, void *stream, void *user);
+    void *user;
+} lbm_allocator;
+
+/* Constants derived from the parameters (all in lattice units). */
+typedef struct {
+    double nu, kappa, gbeta, tau_f;
+    double s_e, s_q;            /* s_e = s_eps = s_nu = s_pi = 1/tau_f; s_q = s_m */
+    double q_kappa, q_e, q_nu;  /* D3Q7 rates, Sec. 2.3 */
+    double a_T, w0_T, w1_T;     /* D3Q7 constant and weights */
+    double H, U;
+    int64_t nodes;              /* nx ny nz */
+    int64_t device_bytes;       /* device memory held by the context */
+} lbm_constants;
+
+#define LBM_NDIAG 24
+
+/* Global diagnostics (free-fall units, dT = 1), definitions of Secs. 3 and 4:
+ *   E        = 1/2 <|u|^2> / U^2                 (mean kinetic energy, Sec. 3)
+ *   rms_drho = sqrt(<(rho - rho0)^2>)            (Table 3)
+ *   rms_div  = sqrt(<(div u)^2>) H / U           (Table 3)
+ *   Re_rms   = sqrt(<|u|^2>) H / nu, Re_w = sqrt(<w^2>) H / nu      (Sec. 4)
+ *   Nu_vol   = 1 + <w T> H / kappa                                  (Sec. 4)
+ *   Nu_kin   = 1 + <eps_u> H^2 / (kappa U^2), eps_u = nu/2 sum (d_i u_j + d_j u_i)^2
+ *   Nu_th    = <eps_T> H^2 / kappa, eps_T = kappa |grad T|^2        (Sec. 4)
+ *   Nu_face[f] = -H <dT/dn> over the nodes of Dirichlet face f, n into the
+ *              fluid (Nu_overall of Sec. 3, Nu_wall of Sec. 4); 0 elsewhere.
+ *              Side-heated cell: Nu_hot = Nu_face[0], Nu_cold = -Nu_face[1];
+ *              Rayleigh-Benard: Nu_wall = (Nu_face[4] - Nu_face[5]) / 2.
+ *   Nu_link[f] = H/kappa times the mean heat per step that the anti-bounce-
+ *              back links of face f carry into the fluid.
+ * Averages <.> run over the nx ny nz nodes.  Derivatives: central differences
+ * inside, a one-sided second-order stencil through the wall value next to a
+ * no-slip or Dirichlet wall, a zero-gradient stencil next to an adiabatic wall.
+ * The avg_* members use the same formulas on the raw sums averaged over every
+ * sample since the last reset, i.e. volume-and-time averages <.>_{V,t}. */
+typedef struct {
+    int64_t step;      /* time step of the state */
+    int64_t sample_step; /* time step of the last sample (-1: none) */
+    int64_t samples;   /* samples in the time averages */
+    double E, rms_drho, rms_div, Re_rms, Re_w, Nu_vol, Nu_kin, Nu_th;
+    double mean_T, mass, max_u;
+    double Nu_face[6], Nu_link[6];
+    double avg_E, avg_Re_rms, avg_Re_w, avg_Nu_vol, avg_Nu_kin, avg_Nu_th;
+    double avg_Nu_face[6];
+    int64_t nonfinite; /* nodes with a non-finite moment in the last sample */
+    double raw[LBM_NDIAG];
+} lbm_diag;
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* Create a cell on the current CUDA device.  stream: a cudaStream_t (NULL: the
+ * legacy default stream).  alloc: may be NULL.  The state starts at rest,
+ * rho = 1, u = 0, T = 0.  *out receives the
+ * context, owned by the caller until lbm_destroy.  On failure *out is NULL and
+ * lbm_last_error(NULL) describes the error. */
+lbm_status lbm_create(const lbm_params *params, const lbm_allocator *alloc, void *stream,
+                      lbm_ctx **out);
+
+/* Release the context and its device memory.  NULL is ignored. */
+void lbm_destroy(lbm_ctx *ctx);
+
+/* Message of the last failed call on ctx (or of the last failed lbm_create on
+ * this thread when ctx is NULL).  Valid until the next call. */
+const char *lbm_last_error(const lbm_ctx *ctx);
+
+/* Derived constants of the context. */
+lbm_status lbm_get_constants(const lbm_ctx *ctx, lbm_constants *out);
+
+/* Replace the state by the equilibrium populations f^eq(rho, u), g^eq(T, u)
+ * (Sec. 2.2, 2.3) of host fields rho[n], u3[3][n], T[n] (n = nx ny nz).  The
+ * step counter is kept; time averages are not touched. */
+lbm_status lbm_set_fields(lbm_ctx *ctx, const double *rho, const double *u3, const double *T);
+
+/* Replace the state by host populations f19[19][n], g7[7][n]: the
+ * pre-collision populations f_i(x, t) of Eq. MRT and g_i(x, t) of Eq. MRT_T. */
+lbm_status lbm_set_populations(lbm_ctx *ctx, const double *f19, const double *g7);
+
+/* Read the pre-collision populations of the current state (same layout). */
+lbm_status lbm_get_populations(lbm_ctx *ctx, double *f19, double *g7);
+
+/* Read the pre-collision populations of `count` nodes with flat indices
+ * nodes[k] = x + nx (y + ny z) into f19[k][19] and g7[k][7] (node-major). */
+lbm_status lbm_get_populations_at(lbm_ctx *ctx, const int64_t *nodes, int64_t count, double *f19,
+                                  double *g7);
+
+/* Advance n time steps (Eq. MRT and Eq. MRT_T for every node, streaming and
+ * walls included).  Asynchronous.  When diag_every > 0, the diagnostics are
+ * sampled every diag_every steps (on steps that are multiples of it, from the
+ * pre-collision state of that step) and accumulated on the device. */
+lbm_status lbm_step(lbm_ctx *ctx, int64_t n);
+
+/* Moments of the current state into host arrays rho[n], u3[3][n], T[n]:
+ * rho = sum f, u = (sum e f + F/2)/rho, T = sum g (Sec. 2.2, 2.3). */
+lbm_status lbm_moments(lbm_ctx *ctx, double *rho, double *u3, double *T);
+
+/* Sample the diagnostics of the current state now (adds to the averages). */
+lbm_status lbm_sample(lbm_ctx *ctx);
+
+/* Fill *out from the last sample and the accumulated averages; reset the
+ * averages afterwards when reset != 0.  Returns LBM_ERR_DIVERGED (with *out
+ * filled) when the last sample saw a non-finite moment or max |u| > 1/sqrt(3). */
+lbm_status lbm_diagnostics(lbm_ctx *ctx, lbm_diag *out, int reset);
+
+/* Wait for the context's stream. */
+lbm_status lbm_synchronize(lbm_ctx *ctx);
+
+/* Checkpoint: write / read the state (populations, step counter, time
+ * accumulators) to / from a file.  lbm_load requires a context created with
+ * the same lattice, walls and storage; continuing after a load reproduces the
+ * run bit for bit. */
+lbm_status lbm_save(lbm_ctx *ctx, const char *path);
+lbm_status lbm_load(lbm_ctx *ctx, const char *path);
+
+/* Device view of the population storage, for callers that keep data on the
+ * GPU: base pointers of f (19 arrays) and g (7 arrays), elements between
+ * consecutive population arrays, and the element size in bytes.  The layout
+ * of the values depends on the streaming scheme and on the step parity; use
+ * lbm_get_populations to read them in a defined layout. */
+lbm_status lbm_device_view(lbm_ctx *ctx, void **f, void **g, int64_t *stride, int *elem_bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_GB300_H */

@@ -1,0 +1,632 @@
+// Host side of the C ABI declared in include/lbm.h: parameter validation and
+// derivation (Secs. 2.1-2.3), device memory, layout bookkeeping of the AA and
+// pull schemes, launch sequencing, diagnostics finalisation and checkpoints.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "lbm_internal.h"
+
+using namespace lbm;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+const int kMagic = 0x4c424d33; // "LBM3"
+
+} // namespace
+
+struct lbm_ctx {
+    lbm_params p{};
+    lbm_constants c{};
+    Geom G{};
+    Phys P{};
+    float wallT[6]{};
+    int dev = 0;
+    cudaStream_t stream = nullptr;
+    lbm_allocator alloc{};
+    bool have_alloc = false;
+    void *pop = nullptr, *pop2 = nullptr; // population buffer(s): 26 arrays of `stride` elements
+    size_t pop_bytes = 0;
+    float *mom = nullptr;                 // kMomArrays x stride floats
+    size_t mom_bytes = 0;
+    double *dsum = nullptr;               // partial[nblocks][kNDiag], raw[kNDiag], acc[kNDiag + 1]
+    size_t dsum_bytes = 0;
+    int nblocks = 0;
+    int elem = 4;
+    int parity = 0;        // AA: 0 natural (next step even), 1 reversed
+    int64_t step = 0;
+    int64_t sample_step = -1;
+    int block = 256;
+    float *hstage = nullptr; // pinned host staging, grown on demand
+    size_t hstage_bytes = 0;
+    std::string err;
+
+    float *host_stage(size_t bytes) {
+        if (bytes <= hstage_bytes) return hstage;
+        if (hstage) cudaFreeHost(hstage);
+        hstage = nullptr;
+        hstage_bytes = 0;
+        void *ptr = nullptr;
+        if (cudaMallocHost(&ptr, bytes) != cudaSuccess) return nullptr;
+        hstage = static_cast<float *>(ptr);
+        hstage_bytes = bytes;
+        return hstage;
+    }
+
+    void *dalloc(size_t bytes) {
+        if (have_alloc) return alloc.alloc(bytes, stream, alloc.user);
+        void *ptr = nullptr;
+        return cudaMalloc(&ptr, bytes) == cudaSuccess ? ptr : nullptr;
+    }
+    void dfree(void *ptr, size_t bytes) {
+        if (!ptr) return;
+        if (have_alloc) alloc.free(ptr, bytes, stream, alloc.user);
+        else cudaFree(ptr);
+    }
+    double *raw() { return dsum + (size_t)nblocks * kNDiag; }
+    double *acc() { return dsum + (size_t)nblocks * kNDiag + kNDiag; }
+    void *fbase(int which) { return which ? pop2 : pop; }
+    void *gbase(int which) {
+        return static_cast<char *>(which ? pop2 : pop) + (size_t)19 * G.stride * elem;
+    }
+    int layout() const { return p.streaming == LBM_STREAM_PULL2 ? 2 : (parity ? 1 : 0); }
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+lbm_status fail(lbm_ctx *ctx, lbm_status s, const std::string &msg) {
+    if (ctx) ctx->err = msg;
+    else g_create_error = msg;
+    return s;
+}
+
+#define CK(ctx, call)                                                                          \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return fail(ctx, LBM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+// Device staging buffer released on scope exit.
+struct Scratch {
+    lbm_ctx *ctx;
+    void *ptr = nullptr;
+    size_t bytes = 0;
+    Scratch(lbm_ctx *c, size_t b) : ctx(c), bytes(b) { ptr = c->dalloc(b); }
+    ~Scratch() {
+        if (ptr) {
+            cudaStreamSynchronize(ctx->stream);
+            ctx->dfree(ptr, bytes);
+        }
+    }
+};
+
+lbm_status validate_and_derive(const lbm_params &p, lbm_constants &c, std::string &why) {
+    if (p.nx < 3 || p.ny < 3 || p.nz < 3) {
+        why = "every lattice dimension must be >= 3";
+        return LBM_ERR_PARAM;
+    }
+    // 32-bit node indices; wrap-around offsets of a periodic axis span up to the
+    // whole lattice and are 32-bit signed
+    const double nodes = (double)p.nx * p.ny * p.nz;
+    const bool any_periodic = p.wall[0].kind == LBM_WALL_PERIODIC || p.wall[2].kind == LBM_WALL_PERIODIC ||
+                              p.wall[4].kind == LBM_WALL_PERIODIC;
+    if (nodes > (any_periodic ? 2147482624.0 : 4294966272.0)) {
+        why = "lattice too large for 32-bit node indices (2^32 - 1024 nodes, 2^31 - 1024 with a periodic axis)";
+        return LBM_ERR_PARAM;
+    }
+    for (int a = 0; a < 3; ++a) {
+        const int k0 = p.wall[2 * a].kind, k1 = p.wall[2 * a + 1].kind;
+        if (k0 < 0 || k0 > 2 || k1 < 0 || k1 > 2) {
+            why = "unknown wall kind";
+            return LBM_ERR_PARAM;
+        }
+        if ((k0 == LBM_WALL_PERIODIC) != (k1 == LBM_WALL_PERIODIC)) {
+            why = "an axis must be periodic on both faces or on neither";
+            return LBM_ERR_PARAM;
+        }
+    }
+    if (p.storage < 0 || p.storage > 2 || p.streaming < 0 || p.streaming > 1) {
+        why = "unknown storage or streaming scheme";
+        return LBM_ERR_PARAM;
+    }
+    if (p.block_size != 0 && (p.block_size < 32 || p.block_size > 256 || p.block_size % 32)) {
+        why = "block_size must be 0 or a multiple of 32 in [32, 256]";
+        return LBM_ERR_PARAM;
+    }
+    if (p.diag_every < 0) {
+        why = "diag_every must be >= 0";
+        return LBM_ERR_PARAM;
+    }
+    if (!(p.U > 0.0 && p.U <= 0.2)) {
+        why = "U must lie in (0, 0.2]";
+        return LBM_ERR_PARAM;
+    }
+    const double H = p.H > 0 ? p.H : (double)p.nz;
+    double nu, kappa, gbeta;
+    if (p.derive) {
+        if (!(p.Ra > 0 && p.Pr > 0)) {
+            why = "Ra and Pr must be positive";
+            return LBM_ERR_PARAM;
+        }
+        // free-fall scaling, Sec. 2.1 (dT = 1)
+        nu = p.U * H * std::sqrt(p.Pr / p.Ra);
+        kappa = nu / p.Pr;
+        gbeta = p.U * p.U / H;
+    } else {
+        nu = p.nu;
+        kappa = p.kappa;
+        gbeta = p.gbeta;
+    }
+    // Sec. 2.2: nu = c_s^2 (tau_f - 1/2), s_e = 1/tau_f, s_q = 8 (2 tau_f - 1)/(8 tau_f - 1)
+    const double tau = 3.0 * nu + 0.5;
+    if (!(tau > 0.5) || !std::isfinite(tau)) {
+        why = "tau_f = 3 nu + 1/2 must exceed 1/2";
+        return LBM_ERR_PARAM;
+    }
+    // Sec. 2.3: q_kappa = 3 - sqrt3, q_e = q_nu = 4 sqrt3 - 6, a_T = 42 sqrt3 kappa - 6
+    const double s3 = std::sqrt(3.0);
+    const double aT = 42.0 * s3 * kappa - 6.0;
+    if (!(aT > -6.0 && aT < 1.0)) {
+        why = "a_T = 42 sqrt(3) kappa - 6 must lie in (-6, 1), i.e. 0 < kappa < 1/(6 sqrt 3)";
+        return LBM_ERR_PARAM;
+    }
+    c.nu = nu;
+    c.kappa = kappa;
+    c.gbeta = gbeta;
+    c.tau_f = tau;
+    c.s_e = 1.0 / tau;
+    c.s_q = 8.0 * (2.0 * tau - 1.0) / (8.0 * tau - 1.0);
+    c.q_kappa = 3.0 - s3;
+    c.q_e = c.q_nu = 4.0 * s3 - 6.0;
+    c.a_T = aT;
+    c.w0_T = (1.0 - aT) / 7.0;
+    c.w1_T = (6.0 + aT) / 42.0;
+    c.H = H;
+    c.U = p.U;
+    c.nodes = (int64_t)p.nx * p.ny * p.nz;
+    return LBM_OK;
+}
+
+uint64_t magic_of(uint32_t d) { return UINT64_MAX / d + 1; }
+
+void finalize(const lbm_ctx *ctx, const double *r, double &E, double &rms_drho, double &rms_div,
+              double &Re, double &Rew, double &Nuv, double &Nuk, double &Nut, double *Nuf,
+              double *Nul) {
+    const double n = r[0] > 0 ? r[0] : 1.0;
+    const double H = ctx->c.H, U = ctx->c.U, nu = ctx->c.nu, ka = ctx->c.kappa;
+    const double area[6] = {(double)ctx->p.ny * ctx->p.nz, (double)ctx->p.ny * ctx->p.nz,
+                            (double)ctx->p.nx * ctx->p.nz, (double)ctx->p.nx * ctx->p.nz,
+                            (double)ctx->p.nx * ctx->p.ny, (double)ctx->p.nx * ctx->p.ny};
+    rms_drho = std::sqrt(r[1] / n);
+    E = 0.5 * r[2] / n / (U * U);
+    Re = std::sqrt(r[2] / n) * H / nu;
+    Rew = std::sqrt(r[3] / n) * H / nu;
+    Nuv = 1.0 + r[4] / n * H / ka;
+    Nuk = 1.0 + nu * r[5] / n * H * H / (ka * U * U);
+    Nut = r[6] / n * H * H;
+    rms_div = std::sqrt(r[7] / n) * H / U;
+    for (int f = 0; f < 6; ++f) {
+        if (Nuf) Nuf[f] = H * r[8 + f] / area[f];
+        if (Nul) Nul[f] = r[18 + f] / area[f] * H / ka;
+    }
+}
+
+lbm_status release(lbm_ctx *ctx) {
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    ctx->dfree(ctx->pop, ctx->pop_bytes);
+    ctx->dfree(ctx->pop2, ctx->pop_bytes);
+    ctx->dfree(ctx->mom, ctx->mom_bytes);
+    ctx->dfree(ctx->dsum, ctx->dsum_bytes);
+    ctx->pop = ctx->pop2 = nullptr;
+    ctx->mom = nullptr;
+    ctx->dsum = nullptr;
+    if (ctx->hstage) cudaFreeHost(ctx->hstage);
+    ctx->hstage = nullptr;
+    ctx->hstage_bytes = 0;
+    return LBM_OK;
+}
+
+// Natural-order float populations [26][n] at host -> device layout.
+lbm_status upload_natural(lbm_ctx *ctx, const float *host) {
+    const size_t bytes = (size_t)26 * (size_t)ctx->c.nodes * sizeof(float);
+    Scratch st(ctx, bytes);
+    if (!st.ptr) return fail(ctx, LBM_ERR_OOM, "staging allocation failed");
+    CK(ctx, cudaMemcpyAsync(st.ptr, host, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    int which = 0;
+    if (ctx->p.streaming == LBM_STREAM_AA) ctx->parity = 0;
+    const int layout = ctx->p.streaming == LBM_STREAM_PULL2 ? 2 : 0;
+    CK(ctx, launch_convert(ctx->p.storage, 0, (float *)st.ptr, ctx->fbase(which), ctx->gbase(which),
+                           ctx->G, ctx->P, layout, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return LBM_OK;
+}
+
+lbm_status sample_into(lbm_ctx *ctx) {
+    CK(ctx, launch_diag(ctx->mom, ctx->G, ctx->P, ctx->wallT, ctx->dsum, ctx->nblocks, ctx->raw(),
+                        ctx->acc(), ctx->stream));
+    ctx->sample_step = ctx->step;
+    return LBM_OK;
+}
+
+} // namespace
+
+extern "C" {
+
+lbm_status lbm_create(const lbm_params *params, const lbm_allocator *alloc, void *stream, lbm_ctx **out) {
+    if (!out) return fail(nullptr, LBM_ERR_PARAM, "out is NULL");
+    *out = nullptr;
+    if (!params) return fail(nullptr, LBM_ERR_PARAM, "params is NULL");
+    lbm_constants c{};
+    std::string why;
+    if (validate_and_derive(*params, c, why) != LBM_OK) return fail(nullptr, LBM_ERR_PARAM, why);
+    if (alloc && (!alloc->alloc || !alloc->free))
+        return fail(nullptr, LBM_ERR_PARAM, "allocator needs both alloc and free");
+
+    lbm_ctx *ctx = new lbm_ctx();
+    ctx->p = *params;
+    ctx->c = c;
+    if (alloc) {
+        ctx->alloc = *alloc;
+        ctx->have_alloc = true;
+    }
+    ctx->stream = static_cast<cudaStream_t>(stream);
+    if (cudaGetDevice(&ctx->dev) != cudaSuccess) {
+        delete ctx;
+        return fail(nullptr, LBM_ERR_CUDA, "no CUDA device");
+    }
+    ctx->block = params->block_size ? params->block_size : 256;
+    ctx->elem = params->storage == LBM_FP32 ? 4 : 2;
+
+    Geom &G = ctx->G;
+    G.nx = params->nx;
+    G.ny = params->ny;
+    G.nz = params->nz;
+    G.n = (uint32_t)c.nodes;
+    G.nxy = (uint32_t)params->nx * (uint32_t)params->ny;
+    G.stride = (c.nodes + 127) / 128 * 128;
+    G.mag_nx = magic_of((uint32_t)params->nx);
+    G.mag_nxy = magic_of(G.nxy);
+    G.periodic = 0;
+    for (int a = 0; a < 3; ++a)
+        if (params->wall[2 * a].kind == LBM_WALL_PERIODIC) G.periodic |= 1 << a;
+
+    Phys &P = ctx->P;
+    P.s_e = (float)c.s_e;
+    P.s_q = (float)c.s_q;
+    P.q_k = (float)c.q_kappa;
+    P.q_e = (float)c.q_e;
+    P.a_T = (float)c.a_T;
+    P.gbeta = (float)c.gbeta;
+    for (int a = 0; a < 3; ++a) P.bf[a] = (float)params->body_force[a];
+    P.dir_mask = 0;
+    for (int f = 0; f < 6; ++f) {
+        const bool dir = params->wall[f].kind == LBM_WALL_DIRICHLET;
+        ctx->wallT[f] = dir ? (float)params->wall[f].T_w : 0.f;
+        P.abbT[f] = dir ? (float)((6.0 + c.a_T) / 21.0 * params->wall[f].T_w) : 0.f;
+        if (dir) P.dir_mask |= 1 << f;
+    }
+
+    ctx->pop_bytes = (size_t)26 * G.stride * ctx->elem;
+    ctx->mom_bytes = (size_t)kMomArrays * G.stride * sizeof(float);
+    ctx->nblocks = diag_blocks(G);
+    ctx->dsum_bytes = ((size_t)ctx->nblocks * kNDiag + 2 * kNDiag + 1) * sizeof(double);
+    ctx->pop = ctx->dalloc(ctx->pop_bytes);
+    if (params->streaming == LBM_STREAM_PULL2) ctx->pop2 = ctx->dalloc(ctx->pop_bytes);
+    ctx->mom = (float *)ctx->dalloc(ctx->mom_bytes);
+    ctx->dsum = (double *)ctx->dalloc(ctx->dsum_bytes);
+    if (!ctx->pop || !ctx->mom || !ctx->dsum || (params->streaming == LBM_STREAM_PULL2 && !ctx->pop2)) {
+        release(ctx);
+        delete ctx;
+        return fail(nullptr, LBM_ERR_OOM, "device allocation failed");
+    }
+    ctx->c.device_bytes = (int64_t)(ctx->pop_bytes * (ctx->pop2 ? 2 : 1) + ctx->mom_bytes + ctx->dsum_bytes);
+    // rest state: all deviations zero (f = w rho0, g = 0); pad entries zero too
+    cudaError_t e = cudaMemsetAsync(ctx->pop, 0, ctx->pop_bytes, ctx->stream);
+    if (e == cudaSuccess && ctx->pop2) e = cudaMemsetAsync(ctx->pop2, 0, ctx->pop_bytes, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->mom, 0, ctx->mom_bytes, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->dsum, 0, ctx->dsum_bytes, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+        release(ctx);
+        delete ctx;
+        return fail(nullptr, LBM_ERR_CUDA, std::string("initialisation: ") + cudaGetErrorString(e));
+    }
+    if (params->streaming == LBM_STREAM_PULL2) {
+        // the pull layout stores wall links as reflected values: load the rest
+        // state through the layout conversion so that T = 0 next to walls too
+        std::vector<float> zero((size_t)26 * (size_t)c.nodes, 0.f);
+        if (upload_natural(ctx, zero.data()) != LBM_OK) {
+            g_create_error = ctx->err;
+            release(ctx);
+            delete ctx;
+            return LBM_ERR_CUDA;
+        }
+    }
+    *out = ctx;
+    return LBM_OK;
+}
+
+void lbm_destroy(lbm_ctx *ctx) {
+    if (!ctx) return;
+    DeviceGuard dg(ctx->dev);
+    release(ctx);
+    delete ctx;
+}
+
+const char *lbm_last_error(const lbm_ctx *ctx) {
+    return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+lbm_status lbm_get_constants(const lbm_ctx *ctx, lbm_constants *out) {
+    if (!ctx || !out) return LBM_ERR_PARAM;
+    *out = ctx->c;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_populations(lbm_ctx *ctx, const double *f19, const double *g7) {
+    if (!ctx || !f19 || !g7) return ctx ? fail(ctx, LBM_ERR_PARAM, "NULL array") : LBM_ERR_PARAM;
+    DeviceGuard dg(ctx->dev);
+    const size_t n = (size_t)ctx->c.nodes;
+    float *host = ctx->host_stage((size_t)26 * n * sizeof(float));
+    if (!host) return fail(ctx, LBM_ERR_OOM, "pinned host staging allocation failed");
+    CK(ctx, cudaStreamSynchronize(ctx->stream)); // the staging may still feed an earlier copy
+    for (int i = 0; i < 19; ++i) {
+        const double w = i == 0 ? 1.0 / 3.0 : (i < 7 ? 1.0 / 18.0 : 1.0 / 36.0);
+        for (size_t k = 0; k < n; ++k) host[i * n + k] = (float)(f19[i * n + k] - w);
+    }
+    for (int i = 0; i < 7; ++i)
+        for (size_t k = 0; k < n; ++k) host[(19 + i) * n + k] = (float)g7[i * n + k];
+    return upload_natural(ctx, host);
+}
+
+lbm_status lbm_set_fields(lbm_ctx *ctx, const double *rho, const double *u3, const double *T) {
+    if (!ctx || !rho || !u3 || !T) return ctx ? fail(ctx, LBM_ERR_PARAM, "NULL array") : LBM_ERR_PARAM;
+    DeviceGuard dg(ctx->dev);
+    const size_t n = (size_t)ctx->c.nodes;
+    float *fields = ctx->host_stage(5 * n * sizeof(float));
+    if (!fields) return fail(ctx, LBM_ERR_OOM, "pinned host staging allocation failed");
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    for (size_t k = 0; k < n; ++k) {
+        fields[k] = (float)(rho[k] - 1.0);
+        fields[n + k] = (float)u3[k];
+        fields[2 * n + k] = (float)u3[n + k];
+        fields[3 * n + k] = (float)u3[2 * n + k];
+        fields[4 * n + k] = (float)T[k];
+    }
+    Scratch fd(ctx, 5 * n * sizeof(float));
+    Scratch st(ctx, (size_t)26 * n * sizeof(float));
+    if (!fd.ptr || !st.ptr) return fail(ctx, LBM_ERR_OOM, "staging allocation failed");
+    CK(ctx, cudaMemcpyAsync(fd.ptr, fields, 5 * n * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    CK(ctx, launch_equilibrium((float *)st.ptr, (const float *)fd.ptr, (uint32_t)n, ctx->P, ctx->stream));
+    if (ctx->p.streaming == LBM_STREAM_AA) ctx->parity = 0;
+    const int layout = ctx->p.streaming == LBM_STREAM_PULL2 ? 2 : 0;
+    CK(ctx, launch_convert(ctx->p.storage, 0, (float *)st.ptr, ctx->fbase(0), ctx->gbase(0), ctx->G,
+                           ctx->P, layout, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_get_populations(lbm_ctx *ctx, double *f19, double *g7) {
+    if (!ctx || !f19 || !g7) return ctx ? fail(ctx, LBM_ERR_PARAM, "NULL array") : LBM_ERR_PARAM;
+    DeviceGuard dg(ctx->dev);
+    const size_t n = (size_t)ctx->c.nodes;
+    Scratch st(ctx, (size_t)26 * n * sizeof(float));
+    if (!st.ptr) return fail(ctx, LBM_ERR_OOM, "staging allocation failed");
+    CK(ctx, launch_convert(ctx->p.storage, 1, (float *)st.ptr, ctx->fbase(0), ctx->gbase(0), ctx->G,
+                           ctx->P, ctx->layout(), ctx->stream));
+    float *host = ctx->host_stage((size_t)26 * n * sizeof(float));
+    if (!host) return fail(ctx, LBM_ERR_OOM, "pinned host staging allocation failed");
+    CK(ctx, cudaMemcpyAsync(host, st.ptr, (size_t)26 * n * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int i = 0; i < 19; ++i) {
+        const double w = i == 0 ? 1.0 / 3.0 : (i < 7 ? 1.0 / 18.0 : 1.0 / 36.0);
+        for (size_t k = 0; k < n; ++k) f19[i * n + k] = (double)host[i * n + k] + w;
+    }
+    for (int i = 0; i < 7; ++i)
+        for (size_t k = 0; k < n; ++k) g7[i * n + k] = (double)host[(19 + i) * n + k];
+    return LBM_OK;
+}
+
+lbm_status lbm_get_populations_at(lbm_ctx *ctx, const int64_t *nodes, int64_t count, double *f19,
+                                  double *g7) {
+    if (!ctx) return LBM_ERR_PARAM;
+    if (count < 0 || (count > 0 && (!nodes || !f19 || !g7))) return fail(ctx, LBM_ERR_PARAM, "bad arguments");
+    if (count == 0) return LBM_OK;
+    for (int64_t k = 0; k < count; ++k)
+        if (nodes[k] < 0 || nodes[k] >= ctx->c.nodes) return fail(ctx, LBM_ERR_PARAM, "node index out of range");
+    DeviceGuard dg(ctx->dev);
+    Scratch dn(ctx, (size_t)count * sizeof(int64_t));
+    Scratch dout(ctx, (size_t)count * 26 * sizeof(float));
+    if (!dn.ptr || !dout.ptr) return fail(ctx, LBM_ERR_OOM, "staging allocation failed");
+    CK(ctx, cudaMemcpyAsync(dn.ptr, nodes, count * sizeof(int64_t), cudaMemcpyHostToDevice, ctx->stream));
+    CK(ctx, launch_gather(ctx->p.storage, (float *)dout.ptr, (const int64_t *)dn.ptr, count, ctx->fbase(0),
+                          ctx->gbase(0), ctx->G, ctx->P, ctx->layout(), ctx->stream));
+    std::vector<float> host((size_t)count * 26);
+    CK(ctx, cudaMemcpyAsync(host.data(), dout.ptr, host.size() * sizeof(float), cudaMemcpyDeviceToHost,
+                            ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int64_t k = 0; k < count; ++k) {
+        for (int i = 0; i < 19; ++i) {
+            const double w = i == 0 ? 1.0 / 3.0 : (i < 7 ? 1.0 / 18.0 : 1.0 / 36.0);
+            f19[k * 19 + i] = (double)host[k * 26 + i] + w;
+        }
+        for (int i = 0; i < 7; ++i) g7[k * 7 + i] = (double)host[k * 26 + 19 + i];
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_ctx *ctx, int64_t nsteps) {
+    if (!ctx) return LBM_ERR_PARAM;
+    if (nsteps < 0) return fail(ctx, LBM_ERR_PARAM, "negative step count");
+    DeviceGuard dg(ctx->dev);
+    StepArgs a{};
+    a.storage = ctx->p.storage;
+    a.scheme = ctx->p.streaming == LBM_STREAM_PULL2 ? 1 : 0;
+    a.block = ctx->block;
+    a.G = ctx->G;
+    a.P = ctx->P;
+    a.stream = ctx->stream;
+    for (int64_t t = 0; t < nsteps; ++t) {
+        const bool sample = ctx->p.diag_every > 0 && ctx->step % ctx->p.diag_every == 0;
+        a.mom = sample ? ctx->mom : nullptr;
+        a.parity = ctx->parity;
+        a.f = ctx->fbase(0);
+        a.g = ctx->gbase(0);
+        a.f2 = ctx->fbase(1);
+        a.g2 = ctx->gbase(1);
+        CK(ctx, launch_step(a));
+        if (sample) {
+            lbm_status s = sample_into(ctx);
+            if (s != LBM_OK) return s;
+        }
+        if (a.scheme == 0) ctx->parity ^= 1;
+        else std::swap(ctx->pop, ctx->pop2);
+        ctx->step += 1;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_moments(lbm_ctx *ctx, double *rho, double *u3, double *T) {
+    if (!ctx || !rho || !u3 || !T) return ctx ? fail(ctx, LBM_ERR_PARAM, "NULL array") : LBM_ERR_PARAM;
+    DeviceGuard dg(ctx->dev);
+    CK(ctx, launch_convert(ctx->p.storage, 2, ctx->mom, ctx->fbase(0), ctx->gbase(0), ctx->G, ctx->P,
+                           ctx->layout(), ctx->stream));
+    const size_t n = (size_t)ctx->c.nodes, s = (size_t)ctx->G.stride;
+    float *host = ctx->host_stage(5 * s * sizeof(float));
+    if (!host) return fail(ctx, LBM_ERR_OOM, "pinned host staging allocation failed");
+    CK(ctx, cudaMemcpyAsync(host, ctx->mom, 5 * s * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    for (size_t k = 0; k < n; ++k) {
+        rho[k] = 1.0 + (double)host[k];
+        u3[k] = host[s + k];
+        u3[n + k] = host[2 * s + k];
+        u3[2 * n + k] = host[3 * s + k];
+        T[k] = host[4 * s + k];
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_sample(lbm_ctx *ctx) {
+    if (!ctx) return LBM_ERR_PARAM;
+    DeviceGuard dg(ctx->dev);
+    CK(ctx, launch_convert(ctx->p.storage, 2, ctx->mom, ctx->fbase(0), ctx->gbase(0), ctx->G, ctx->P,
+                           ctx->layout(), ctx->stream));
+    return sample_into(ctx);
+}
+
+lbm_status lbm_diagnostics(lbm_ctx *ctx, lbm_diag *out, int reset) {
+    if (!ctx || !out) return ctx ? fail(ctx, LBM_ERR_PARAM, "out is NULL") : LBM_ERR_PARAM;
+    DeviceGuard dg(ctx->dev);
+    double host[2 * kNDiag + 1];
+    CK(ctx, cudaMemcpyAsync(host, ctx->raw(), sizeof(host), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    std::memset(out, 0, sizeof(*out));
+    const double *raw = host, *acc = host + kNDiag;
+    const double ns = acc[kNDiag];
+    out->step = ctx->step;
+    out->sample_step = ctx->sample_step;
+    out->samples = (int64_t)ns;
+    finalize(ctx, raw, out->E, out->rms_drho, out->rms_div, out->Re_rms, out->Re_w, out->Nu_vol, out->Nu_kin,
+             out->Nu_th, out->Nu_face, out->Nu_link);
+    out->mean_T = raw[0] > 0 ? raw[14] / raw[0] : 0.0;
+    out->mass = raw[15];
+    out->max_u = raw[16];
+    out->nonfinite = (int64_t)raw[17];
+    for (int k = 0; k < kNDiag; ++k) out->raw[k] = raw[k];
+    if (ns > 0) {
+        double avg[kNDiag];
+        for (int k = 0; k < kNDiag; ++k) avg[k] = k == 16 ? acc[k] : acc[k] / ns;
+        double d1, d2;
+        finalize(ctx, avg, out->avg_E, d1, d2, out->avg_Re_rms, out->avg_Re_w, out->avg_Nu_vol, out->avg_Nu_kin,
+                 out->avg_Nu_th, out->avg_Nu_face, nullptr);
+    }
+    if (reset) {
+        CK(ctx, cudaMemsetAsync(ctx->acc(), 0, (kNDiag + 1) * sizeof(double), ctx->stream));
+        CK(ctx, cudaStreamSynchronize(ctx->stream));
+    }
+    if (ctx->sample_step >= 0 && (out->nonfinite > 0 || !(out->max_u <= 1.0 / std::sqrt(3.0))))
+        return fail(ctx, LBM_ERR_DIVERGED, "state diverged: non-finite moment or |u| above the sound speed");
+    return LBM_OK;
+}
+
+lbm_status lbm_synchronize(lbm_ctx *ctx) {
+    if (!ctx) return LBM_ERR_PARAM;
+    DeviceGuard dg(ctx->dev);
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return LBM_OK;
+}
+
+struct CkptHeader {
+    int magic, version, nx, ny, nz, storage, streaming, parity;
+    int64_t step, sample_step, stride;
+};
+
+lbm_status lbm_save(lbm_ctx *ctx, const char *path) {
+    if (!ctx || !path) return ctx ? fail(ctx, LBM_ERR_PARAM, "path is NULL") : LBM_ERR_PARAM;
+    DeviceGuard dg(ctx->dev);
+    std::vector<char> pop(ctx->pop_bytes);
+    double sums[2 * kNDiag + 1];
+    CK(ctx, cudaMemcpyAsync(pop.data(), ctx->pop, ctx->pop_bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaMemcpyAsync(sums, ctx->raw(), sizeof(sums), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    FILE *fp = std::fopen(path, "wb");
+    if (!fp) return fail(ctx, LBM_ERR_PARAM, std::string("cannot open ") + path);
+    CkptHeader h{kMagic, 1, ctx->p.nx, ctx->p.ny, ctx->p.nz, ctx->p.storage, ctx->p.streaming, ctx->parity,
+                 ctx->step, ctx->sample_step, ctx->G.stride};
+    bool ok = std::fwrite(&h, sizeof(h), 1, fp) == 1 && std::fwrite(pop.data(), 1, pop.size(), fp) == pop.size() &&
+              std::fwrite(sums, sizeof(sums), 1, fp) == 1;
+    ok = (std::fclose(fp) == 0) && ok;
+    return ok ? LBM_OK : fail(ctx, LBM_ERR_PARAM, std::string("write failed: ") + path);
+}
+
+lbm_status lbm_load(lbm_ctx *ctx, const char *path) {
+    if (!ctx || !path) return ctx ? fail(ctx, LBM_ERR_PARAM, "path is NULL") : LBM_ERR_PARAM;
+    DeviceGuard dg(ctx->dev);
+    FILE *fp = std::fopen(path, "rb");
+    if (!fp) return fail(ctx, LBM_ERR_PARAM, std::string("cannot open ") + path);
+    CkptHeader h{};
+    std::vector<char> pop(ctx->pop_bytes);
+    double sums[2 * kNDiag + 1];
+    bool ok = std::fread(&h, sizeof(h), 1, fp) == 1;
+    ok = ok && h.magic == kMagic && h.version == 1 && h.nx == ctx->p.nx && h.ny == ctx->p.ny &&
+         h.nz == ctx->p.nz && h.storage == ctx->p.storage && h.streaming == ctx->p.streaming &&
+         h.stride == ctx->G.stride;
+    ok = ok && std::fread(pop.data(), 1, pop.size(), fp) == pop.size() && std::fread(sums, sizeof(sums), 1, fp) == 1;
+    std::fclose(fp);
+    if (!ok) return fail(ctx, LBM_ERR_PARAM, std::string("checkpoint does not match this context: ") + path);
+    CK(ctx, cudaMemcpyAsync(ctx->pop, pop.data(), ctx->pop_bytes, cudaMemcpyHostToDevice, ctx->stream));
+    CK(ctx, cudaMemcpyAsync(ctx->raw(), sums, sizeof(sums), cudaMemcpyHostToDevice, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    ctx->parity = h.parity;
+    ctx->step = h.step;
+    ctx->sample_step = h.sample_step;
+    return LBM_OK;
+}
+
+lbm_status lbm_device_view(lbm_ctx *ctx, void **f, void **g, int64_t *stride, int *elem_bytes) {
+    if (!ctx) return LBM_ERR_PARAM;
+    if (f) *f = ctx->fbase(0);
+    if (g) *g = ctx->gbase(0);
+    if (stride) *stride = ctx->G.stride;
+    if (elem_bytes) *elem_bytes = ctx->elem;
+    return LBM_OK;
+}
+
+} // extern "C"

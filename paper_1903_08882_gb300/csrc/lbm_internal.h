@@ -1,0 +1,43 @@
+// Internal interface between the C ABI (lbm_api.cu) and the kernel files.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+constexpr int kNDiag = 24;     // raw diagnostic sums per sample
+constexpr int kMomArrays = 11; // rho - rho0, u, v, w, T, and g arriving from each of the 6 faces
+
+struct StepArgs {
+    int storage;  // StorageKind
+    int scheme;   // 0: AA pattern, 1: two-buffer pull
+    int parity;   // AA: 0 even step (natural -> reversed), 1 odd step
+    int block;    // threads per block
+    void *f, *g;  // AA buffer, or pull source
+    void *f2, *g2; // pull destination
+    Geom G;
+    Phys P;
+    float *mom;   // non-null: also write the node moments of the pre-step state
+    cudaStream_t stream;
+};
+
+cudaError_t launch_step(const StepArgs &a);
+// op 0: staging -> device layout, 1: device layout -> staging, 2: moments -> st
+cudaError_t launch_convert(int storage, int op, float *st, void *f, void *g, const Geom &G,
+                           const Phys &P, int layout, cudaStream_t stream);
+cudaError_t launch_gather(int storage, float *out, const int64_t *nodes, int64_t count, const void *f,
+                          const void *g, const Geom &G, const Phys &P, int layout, cudaStream_t stream);
+cudaError_t launch_equilibrium(float *st, const float *fields, uint32_t n, const Phys &P,
+                               cudaStream_t stream);
+
+// Diagnostics: reduce the moment arrays into per-block partial sums, then sum
+// them into raw[kNDiag] (this sample) and add raw to acc[kNDiag] (time sums;
+// acc[kNDiag] counts the samples).
+int diag_blocks(const Geom &G);
+cudaError_t launch_diag(const float *mom, const Geom &G, const Phys &P, const float *wallT,
+                        double *partial, int nblocks, double *raw, double *acc, cudaStream_t stream);
+
+} // namespace lbm

@@ -1,0 +1,381 @@
+// Time-step kernels of the thermal lattice Boltzmann library and the kernels
+// that move a state between the device layouts and a plain natural layout.
+//
+// One thread updates one node: it loads the 19 + 7 populations arriving at
+// the node, runs the fused D3Q19 + D3Q7 MRT collision (Eq. MRT, Eq. MRT_T)
+// in registers, applies the wall rules of Secs. 2.2-2.3 for links that cross
+// a wall, and stores the 26 post-collision populations.  Population arrays
+// are structure-of-arrays with x fastest, so a warp reads and writes 32
+// consecutive nodes of each array.
+//
+// Device layouts of a state:
+//   LAYOUT_NATURAL   A[i][x] = f_i(x, t), the pre-collision populations.
+//   LAYOUT_REVERSED  A[ibar][x] = f_i+(x, t-1): the AA pattern after an even
+//                    step (post-collision values kept in the opposite slot of
+//                    their own node, not yet streamed).
+//   LAYOUT_PULL      B[i][x] = f_i+(x, t-1): the two-buffer pull scheme.
+// In both post-collision layouts, a link that arrives at x from a wall takes
+// the value that left x towards that wall, f_ibar+(x, t-1) (bounce-back); g
+// takes the same value, or minus it plus (6 + a_T)/21 T_w at a Dirichlet wall
+// (anti-bounce-back).
+#include "lbm_device.cuh"
+#include "lbm_internal.h"
+
+namespace lbm {
+
+enum Layout { LAYOUT_NATURAL = 0, LAYOUT_REVERSED = 1, LAYOUT_PULL = 2 };
+
+template <int S> using SE = typename Store<S>::T;
+
+// Read the pre-collision populations of node (x, y, z) from a device layout.
+template <int S>
+__device__ __forceinline__ void read_natural(const SE<S> *__restrict__ f, const SE<S> *__restrict__ g,
+                                             const Geom &G, const Phys &P, int layout, uint32_t n,
+                                             int x, int y, int z, float (&fl)[19], float (&gl)[7]) {
+    const int64_t s = G.stride;
+    if (layout == LAYOUT_NATURAL) {
+#pragma unroll
+        for (int i = 0; i < 19; ++i) fl[i] = Store<S>::ld(f + i * s + n);
+#pragma unroll
+        for (int i = 0; i < 7; ++i) gl[i] = Store<S>::ld(g + i * s + n);
+        return;
+    }
+    const Nbr b = neighbours(G, x, y, z);
+    const bool rev = layout == LAYOUT_REVERSED;
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        const int slot_in = rev ? opp19(i) : i, slot_wall = rev ? i : opp19(i);
+        if (!src_wall(b, ex19(i), ey19(i), ez19(i)))
+            fl[i] = Store<S>::ld(f + slot_in * s + (int64_t)n + src_off(b, ex19(i), ey19(i), ez19(i)));
+        else
+            fl[i] = Store<S>::ld(f + slot_wall * s + n);
+    }
+#pragma unroll
+    for (int i = 0; i < 7; ++i) {
+        const int slot_in = rev ? opp7(i) : i, slot_wall = rev ? i : opp7(i);
+        if (!src_wall(b, ex7(i), ey7(i), ez7(i))) {
+            gl[i] = Store<S>::ld(g + slot_in * s + (int64_t)n + src_off(b, ex7(i), ey7(i), ez7(i)));
+        } else {
+            const int fc = face_of(-ex7(i), -ey7(i), -ez7(i));
+            const float v = Store<S>::ld(g + slot_wall * s + n);
+            gl[i] = ((P.dir_mask >> fc) & 1) ? P.abbT[fc] - v : v;
+        }
+    }
+}
+
+// Diagnostic sample of one node: moments (rho - rho0, u, v, w, T) of the
+// pre-collision state, and for a node next to a wall on face f the
+// pre-collision g arriving from that wall (velocity index f + 1 points away
+// from face f).  gin holds g before the collision.
+__device__ __forceinline__ void write_sample(float *__restrict__ mom, int64_t s, uint32_t n,
+                                             const Macro &m, const Nbr &b, const float (&gin)[7]) {
+    mom[n] = m.drho;
+    mom[s + n] = m.u;
+    mom[2 * s + n] = m.v;
+    mom[3 * s + n] = m.w;
+    mom[4 * s + n] = m.T;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (b.wm[a]) mom[(5 + 2 * a) * s + n] = gin[2 * a + 1];
+        if (b.wp[a]) mom[(6 + 2 * a) * s + n] = gin[2 * a + 2];
+    }
+}
+
+// ------------------------------------------------------------ AA pattern ----
+
+// Even step: natural -> reversed.  Reads and writes only the node's own slots.
+template <int S, bool MOM>
+__global__ void __launch_bounds__(256) k_aa_even(SE<S> *__restrict__ f, SE<S> *__restrict__ g, Geom G,
+                                                 Phys P, float *__restrict__ mom) {
+    const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= G.n) return;
+    const int64_t s = G.stride;
+    float fl[19], gl[7];
+#pragma unroll
+    for (int i = 0; i < 19; ++i) fl[i] = Store<S>::ld(f + i * s + n);
+#pragma unroll
+    for (int i = 0; i < 7; ++i) gl[i] = Store<S>::ld(g + i * s + n);
+    float g0[7];
+#pragma unroll
+    for (int i = 0; i < 7; ++i) g0[i] = gl[i];
+    const Macro m = collide(P, fl, gl);
+#pragma unroll
+    for (int i = 0; i < 19; ++i) Store<S>::st(f + opp19(i) * s + n, fl[i]);
+#pragma unroll
+    for (int i = 0; i < 7; ++i) Store<S>::st(g + opp7(i) * s + n, gl[i]);
+    if (MOM) {
+        int x, y, z;
+        node_xyz(G, n, x, y, z);
+        write_sample(mom, s, n, m, neighbours(G, x, y, z), g0);
+    }
+}
+
+// Odd step: reversed -> natural.  Gathers f_i+(x - e_i) from the opposite
+// slot of the upstream node and scatters f_i+(x) to slot i of x + e_i; every
+// location a thread reads is written by that same thread only, so the update
+// is in place without a second buffer.
+template <int S, bool MOM>
+__global__ void __launch_bounds__(256) k_aa_odd(SE<S> *__restrict__ f, SE<S> *__restrict__ g, Geom G,
+                                                Phys P, float *__restrict__ mom) {
+    const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= G.n) return;
+    const int64_t s = G.stride;
+    int x, y, z;
+    node_xyz(G, n, x, y, z);
+    const Nbr b = neighbours(G, x, y, z);
+    float fl[19], gl[7];
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        if (!src_wall(b, ex19(i), ey19(i), ez19(i)))
+            fl[i] = Store<S>::ld(f + opp19(i) * s + (int64_t)n + src_off(b, ex19(i), ey19(i), ez19(i)));
+        else
+            fl[i] = Store<S>::ld(f + i * s + n);
+    }
+#pragma unroll
+    for (int i = 0; i < 7; ++i) {
+        if (!src_wall(b, ex7(i), ey7(i), ez7(i))) {
+            gl[i] = Store<S>::ld(g + opp7(i) * s + (int64_t)n + src_off(b, ex7(i), ey7(i), ez7(i)));
+        } else {
+            const int fc = face_of(-ex7(i), -ey7(i), -ez7(i));
+            const float v = Store<S>::ld(g + i * s + n);
+            gl[i] = ((P.dir_mask >> fc) & 1) ? P.abbT[fc] - v : v;
+        }
+    }
+    float g0[7];
+#pragma unroll
+    for (int i = 0; i < 7; ++i) g0[i] = gl[i];
+    const Macro m = collide(P, fl, gl);
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        if (!dst_wall(b, ex19(i), ey19(i), ez19(i)))
+            Store<S>::st(f + i * s + (int64_t)n + dst_off(b, ex19(i), ey19(i), ez19(i)), fl[i]);
+        else
+            Store<S>::st(f + opp19(i) * s + n, fl[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < 7; ++i) {
+        if (!dst_wall(b, ex7(i), ey7(i), ez7(i))) {
+            Store<S>::st(g + i * s + (int64_t)n + dst_off(b, ex7(i), ey7(i), ez7(i)), gl[i]);
+        } else {
+            const int fc = face_of(ex7(i), ey7(i), ez7(i));
+            const float v = gl[i];
+            Store<S>::st(g + opp7(i) * s + n, ((P.dir_mask >> fc) & 1) ? P.abbT[fc] - v : v);
+        }
+    }
+    if (MOM) write_sample(mom, s, n, m, b, g0);
+}
+
+// ------------------------------------------------------ two-buffer pull ----
+
+template <int S, bool MOM>
+__global__ void __launch_bounds__(256) k_pull(const SE<S> *__restrict__ fs, const SE<S> *__restrict__ gs,
+                                              SE<S> *__restrict__ fd, SE<S> *__restrict__ gd, Geom G,
+                                              Phys P, float *__restrict__ mom) {
+    const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= G.n) return;
+    int x, y, z;
+    node_xyz(G, n, x, y, z);
+    float fl[19], gl[7];
+    read_natural<S>(fs, gs, G, P, LAYOUT_PULL, n, x, y, z, fl, gl);
+    float g0[7];
+#pragma unroll
+    for (int i = 0; i < 7; ++i) g0[i] = gl[i];
+    const Macro m = collide(P, fl, gl);
+    const int64_t s = G.stride;
+#pragma unroll
+    for (int i = 0; i < 19; ++i) Store<S>::st(fd + i * s + n, fl[i]);
+#pragma unroll
+    for (int i = 0; i < 7; ++i) Store<S>::st(gd + i * s + n, gl[i]);
+    if (MOM) write_sample(mom, s, n, m, neighbours(G, x, y, z), g0);
+}
+
+// ------------------------------------------------- layout conversions ----
+
+// Natural host-order staging (float, [26][n], no padding) -> device layout.
+// For LAYOUT_PULL, B[j][m] must make the pull reproduce the natural state:
+// B[j][m] = f_j(m + e_j), or, where m + e_j is behind a wall, the value that
+// bounces back into f_jbar(m).
+template <int S>
+__global__ void k_load(const float *__restrict__ st, SE<S> *__restrict__ f, SE<S> *__restrict__ g,
+                       Geom G, Phys P, int layout) {
+    const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= G.n) return;
+    const int64_t s = G.stride, N = G.n;
+    if (layout == LAYOUT_NATURAL) {
+        for (int i = 0; i < 19; ++i) Store<S>::st(f + i * s + n, st[i * N + n]);
+        for (int i = 0; i < 7; ++i) Store<S>::st(g + i * s + n, st[(19 + i) * N + n]);
+        return;
+    }
+    int x, y, z;
+    node_xyz(G, n, x, y, z);
+    const Nbr b = neighbours(G, x, y, z);
+#pragma unroll
+    for (int j = 0; j < 19; ++j) {
+        float v;
+        if (!dst_wall(b, ex19(j), ey19(j), ez19(j)))
+            v = st[j * N + (int64_t)n + dst_off(b, ex19(j), ey19(j), ez19(j))];
+        else
+            v = st[opp19(j) * N + n];
+        Store<S>::st(f + j * s + n, v);
+    }
+#pragma unroll
+    for (int j = 0; j < 7; ++j) {
+        float v;
+        if (!dst_wall(b, ex7(j), ey7(j), ez7(j))) {
+            v = st[(19 + j) * N + (int64_t)n + dst_off(b, ex7(j), ey7(j), ez7(j))];
+        } else {
+            const int fc = face_of(ex7(j), ey7(j), ez7(j));
+            const float gin = st[(19 + opp7(j)) * N + n];
+            v = ((P.dir_mask >> fc) & 1) ? P.abbT[fc] - gin : gin;
+        }
+        Store<S>::st(g + j * s + n, v);
+    }
+}
+
+// Device layout -> natural staging (float [26][n]).
+template <int S>
+__global__ void k_store(float *__restrict__ st, const SE<S> *__restrict__ f, const SE<S> *__restrict__ g,
+                        Geom G, Phys P, int layout) {
+    const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= G.n) return;
+    int x, y, z;
+    node_xyz(G, n, x, y, z);
+    float fl[19], gl[7];
+    read_natural<S>(f, g, G, P, layout, n, x, y, z, fl, gl);
+    const int64_t N = G.n;
+#pragma unroll
+    for (int i = 0; i < 19; ++i) st[i * N + n] = fl[i];
+#pragma unroll
+    for (int i = 0; i < 7; ++i) st[(19 + i) * N + n] = gl[i];
+}
+
+// Pre-collision populations of listed nodes -> out[k][26].
+template <int S>
+__global__ void k_gather(float *__restrict__ out, const int64_t *__restrict__ nodes, int64_t count,
+                         const SE<S> *__restrict__ f, const SE<S> *__restrict__ g, Geom G, Phys P,
+                         int layout) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= count) return;
+    const uint32_t n = static_cast<uint32_t>(nodes[k]);
+    int x, y, z;
+    node_xyz(G, n, x, y, z);
+    float fl[19], gl[7];
+    read_natural<S>(f, g, G, P, layout, n, x, y, z, fl, gl);
+#pragma unroll
+    for (int i = 0; i < 19; ++i) out[k * 26 + i] = fl[i];
+#pragma unroll
+    for (int i = 0; i < 7; ++i) out[k * 26 + 19 + i] = gl[i];
+}
+
+// Diagnostic sample of the state -> mom[11][stride] (see write_sample).
+template <int S>
+__global__ void k_moments(float *__restrict__ mom, const SE<S> *__restrict__ f,
+                          const SE<S> *__restrict__ g, Geom G, Phys P, int layout) {
+    const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= G.n) return;
+    int x, y, z;
+    node_xyz(G, n, x, y, z);
+    float fl[19], gl[7];
+    read_natural<S>(f, g, G, P, layout, n, x, y, z, fl, gl);
+    write_sample(mom, G.stride, n, macro(P, fl, gl), neighbours(G, x, y, z), gl);
+}
+
+// Equilibrium deviations from fields (float [5][n]: rho - rho0, u, v, w, T)
+// into natural staging [26][n]:
+//   f_i^eq - w_i rho0 = w_i [drho + rho (3 e.u + 9/2 (e.u)^2 - 3/2 |u|^2)]
+//   g_i^eq = w_i^T T [1 + 7/(6 + a_T) 3 e.u]            (Sec. 2.2, 2.3)
+__global__ void k_equilibrium(float *__restrict__ st, const float *__restrict__ fields, uint32_t N,
+                              Phys P) {
+    const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const float dr = fields[n], u = fields[N + n], v = fields[2 * (int64_t)N + n];
+    const float w = fields[3 * (int64_t)N + n], T = fields[4 * (int64_t)N + n];
+    const float rho = 1.f + dr, uu = u * u + v * v + w * w;
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        const float eu = ex19(i) * u + ey19(i) * v + ez19(i) * w;
+        st[i * (int64_t)N + n] = w19(i) * (dr + rho * (3.f * eu + 4.5f * eu * eu - 1.5f * uu));
+    }
+    const float w0 = (1.f - P.a_T) / 7.f, w1 = (6.f + P.a_T) / 42.f, c = 21.f / (6.f + P.a_T);
+#pragma unroll
+    for (int i = 0; i < 7; ++i) {
+        const float eu = ex7(i) * u + ey7(i) * v + ez7(i) * w;
+        st[(19 + i) * (int64_t)N + n] = (i == 0 ? w0 : w1) * T * (1.f + c * eu);
+    }
+}
+
+// ---------------------------------------------------------- launchers ----
+
+static inline unsigned blocks_for(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+template <int S>
+static cudaError_t step_t(const StepArgs &a) {
+    const unsigned nb = blocks_for(a.G.n, a.block);
+    auto f = static_cast<SE<S> *>(a.f), g = static_cast<SE<S> *>(a.g);
+    if (a.scheme == 0) {
+        if (a.parity == 0) {
+            if (a.mom) k_aa_even<S, true><<<nb, a.block, 0, a.stream>>>(f, g, a.G, a.P, a.mom);
+            else k_aa_even<S, false><<<nb, a.block, 0, a.stream>>>(f, g, a.G, a.P, nullptr);
+        } else {
+            if (a.mom) k_aa_odd<S, true><<<nb, a.block, 0, a.stream>>>(f, g, a.G, a.P, a.mom);
+            else k_aa_odd<S, false><<<nb, a.block, 0, a.stream>>>(f, g, a.G, a.P, nullptr);
+        }
+    } else {
+        auto f2 = static_cast<SE<S> *>(a.f2), g2 = static_cast<SE<S> *>(a.g2);
+        if (a.mom) k_pull<S, true><<<nb, a.block, 0, a.stream>>>(f, g, f2, g2, a.G, a.P, a.mom);
+        else k_pull<S, false><<<nb, a.block, 0, a.stream>>>(f, g, f2, g2, a.G, a.P, nullptr);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step(const StepArgs &a) {
+    switch (a.storage) {
+    case ST_F32: return step_t<ST_F32>(a);
+    case ST_F16: return step_t<ST_F16>(a);
+    default: return step_t<ST_BF16>(a);
+    }
+}
+
+template <int S>
+static cudaError_t convert_t(int op, float *st, void *f, void *g, const Geom &G, const Phys &P,
+                             int layout, cudaStream_t stream) {
+    const unsigned nb = blocks_for(G.n, 256);
+    if (op == 0) k_load<S><<<nb, 256, 0, stream>>>(st, (SE<S> *)f, (SE<S> *)g, G, P, layout);
+    else if (op == 1) k_store<S><<<nb, 256, 0, stream>>>(st, (const SE<S> *)f, (const SE<S> *)g, G, P, layout);
+    else k_moments<S><<<nb, 256, 0, stream>>>(st, (const SE<S> *)f, (const SE<S> *)g, G, P, layout);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_convert(int storage, int op, float *st, void *f, void *g, const Geom &G,
+                           const Phys &P, int layout, cudaStream_t stream) {
+    switch (storage) {
+    case ST_F32: return convert_t<ST_F32>(op, st, f, g, G, P, layout, stream);
+    case ST_F16: return convert_t<ST_F16>(op, st, f, g, G, P, layout, stream);
+    default: return convert_t<ST_BF16>(op, st, f, g, G, P, layout, stream);
+    }
+}
+
+cudaError_t launch_gather(int storage, float *out, const int64_t *nodes, int64_t count, const void *f,
+                          const void *g, const Geom &G, const Phys &P, int layout, cudaStream_t stream) {
+    const unsigned nb = blocks_for(count, 128);
+    switch (storage) {
+    case ST_F32:
+        k_gather<ST_F32><<<nb, 128, 0, stream>>>(out, nodes, count, (const float *)f, (const float *)g, G, P, layout);
+        break;
+    case ST_F16:
+        k_gather<ST_F16><<<nb, 128, 0, stream>>>(out, nodes, count, (const __half *)f, (const __half *)g, G, P, layout);
+        break;
+    default:
+        k_gather<ST_BF16><<<nb, 128, 0, stream>>>(out, nodes, count, (const __nv_bfloat16 *)f,
+                                                  (const __nv_bfloat16 *)g, G, P, layout);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_equilibrium(float *st, const float *fields, uint32_t n, const Phys &P,
+                               cudaStream_t stream) {
+    k_equilibrium<<<blocks_for(n, 256), 256, 0, stream>>>(st, fields, n, P);
+    return cudaGetLastError();
+}
+
+} // namespace lbm

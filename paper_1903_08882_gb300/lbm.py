@@ -1,0 +1,386 @@
+"""Python binding of the C ABI declared in include/lbm.h.
+
+Argument marshalling only: every step of the method runs in the CUDA library
+liblbm_gb300.so.  There is no Python or CPU fallback; if the library is
+missing, loading it raises.  Device memory is provided by PyTorch's caching
+allocator through the lbm_allocator hook; streams are PyTorch streams.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "liblbm_gb300.so")
+
+LBM_OK, LBM_ERR_PARAM, LBM_ERR_CUDA, LBM_ERR_OOM, LBM_ERR_DIVERGED, LBM_ERR_TIMEOUT, LBM_ERR_STATE = range(7)
+ADIABATIC, DIRICHLET, PERIODIC = 0, 1, 2
+STORAGE = {"fp32": 0, "fp16s": 1, "bf16s": 2}
+STREAMING = {"aa": 0, "pull2": 1}
+NDIAG = 24
+
+c_int, c_double, c_int64, c_void_p, c_size_t = (ctypes.c_int, ctypes.c_double, ctypes.c_int64,
+                                                 ctypes.c_void_p, ctypes.c_size_t)
+
+
+class LbmWall(ctypes.Structure):
+    _fields_ = [("kind", c_int), ("T_w", c_double)]
+
+
+class LbmParams(ctypes.Structure):
+    _fields_ = [
+        ("nx", c_int), ("ny", c_int), ("nz", c_int),
+        ("Ra", c_double), ("Pr", c_double), ("U", c_double), ("H", c_double),
+        ("derive", c_int),
+        ("nu", c_double), ("kappa", c_double), ("gbeta", c_double),
+        ("body_force", c_double * 3),
+        ("wall", LbmWall * 6),
+        ("storage", c_int), ("streaming", c_int), ("diag_every", c_int), ("block_size", c_int),
+    ]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(c_void_p, c_size_t, c_void_p, c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, c_void_p, c_size_t, c_void_p, c_void_p)
+
+
+class LbmAllocator(ctypes.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("user", c_void_p)]
+
+
+class LbmConstants(ctypes.Structure):
+    _fields_ = [(k, c_double) for k in ("nu", "kappa", "gbeta", "tau_f", "s_e", "s_q", "q_kappa", "q_e",
+                                         "q_nu", "a_T", "w0_T", "w1_T", "H", "U")] + [
+        ("nodes", c_int64), ("device_bytes", c_int64)]
+
+
+class LbmDiag(ctypes.Structure):
+    _fields_ = ([("step", c_int64), ("sample_step", c_int64), ("samples", c_int64)]
+                + [(k, c_double) for k in ("E", "rms_drho", "rms_div", "Re_rms", "Re_w", "Nu_vol", "Nu_kin",
+                                           "Nu_th", "mean_T", "mass", "max_u")]
+                + [("Nu_face", c_double * 6), ("Nu_link", c_double * 6)]
+                + [(k, c_double) for k in ("avg_E", "avg_Re_rms", "avg_Re_w", "avg_Nu_vol", "avg_Nu_kin",
+                                           "avg_Nu_th")]
+                + [("avg_Nu_face", c_double * 6), ("nonfinite", c_int64), ("raw", c_double * NDIAG)])
+
+    def as_dict(self) -> dict:
+        out = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            out[name] = np.array(v[:]) if isinstance(v, ctypes.Array) else v
+        return out
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status: int, message: str, diag: dict | None = None):
+        super().__init__(f"lbm status {status}: {message}")
+        self.status = status
+        self.diag = diag
+
+
+_lib = None
+
+
+def lib():
+    """The loaded CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() (nvcc, sm_103a)")
+    L = ctypes.CDLL(LIB_PATH)
+    P, C = ctypes.POINTER, ctypes.POINTER(ctypes.c_void_p)
+    dp, i64p = P(c_double), P(c_int64)
+    sig = {
+        "lbm_create": ([P(LbmParams), P(LbmAllocator), c_void_p, C], c_int),
+        "lbm_destroy": ([c_void_p], None),
+        "lbm_last_error": ([c_void_p], ctypes.c_char_p),
+        "lbm_get_constants": ([c_void_p, P(LbmConstants)], c_int),
+        "lbm_set_fields": ([c_void_p, dp, dp, dp], c_int),
+        "lbm_set_populations": ([c_void_p, dp, dp], c_int),
+        "lbm_get_populations": ([c_void_p, dp, dp], c_int),
+        "lbm_get_populations_at": ([c_void_p, i64p, c_int64, dp, dp], c_int),
+        "lbm_step": ([c_void_p, c_int64], c_int),
+        "lbm_moments": ([c_void_p, dp, dp, dp], c_int),
+        "lbm_sample": ([c_void_p], c_int),
+        "lbm_diagnostics": ([c_void_p, P(LbmDiag), c_int], c_int),
+        "lbm_synchronize": ([c_void_p], c_int),
+        "lbm_save": ([c_void_p, ctypes.c_char_p], c_int),
+        "lbm_load": ([c_void_p, ctypes.c_char_p], c_int),
+        "lbm_device_view": ([c_void_p, C, C, i64p, P(c_int)], c_int),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = L
+    return L
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(c_double))
+
+
+def _f64(a, shape):
+    a = np.ascontiguousarray(np.broadcast_to(np.asarray(a, dtype=np.float64), shape))
+    return a
+
+
+# ------------------------------------------------------------- allocator --
+
+_torch_alloc = None
+
+
+def torch_allocator() -> LbmAllocator:
+    """An lbm_allocator backed by PyTorch's CUDA caching allocator."""
+    global _torch_alloc
+    if _torch_alloc is None:
+        import torch
+
+        def _alloc(nbytes, stream, user):
+            try:
+                return torch.cuda.caching_allocator_alloc(int(nbytes), stream=int(stream or 0))
+            except Exception:  # out of memory: the library reports LBM_ERR_OOM
+                return None
+
+        def _free(ptr, nbytes, stream, user):
+            try:
+                torch.cuda.caching_allocator_delete(int(ptr))
+            except Exception:
+                pass
+
+        a = LbmAllocator()
+        a.alloc = ALLOC_FN(_alloc)
+        a.free = FREE_FN(_free)
+        a.user = None
+        _torch_alloc = a
+    return _torch_alloc
+
+
+# ---------------------------------------------------------------- params --
+
+def walls_side_heated(T_hot=0.5, T_cold=-0.5):
+    """Hot face -x, cold face +x, four adiabatic faces (all no-slip)."""
+    return [(DIRICHLET, T_hot), (DIRICHLET, T_cold)] + [(ADIABATIC, 0.0)] * 4
+
+
+def walls_rayleigh_benard(T_bottom=0.5, T_top=-0.5):
+    """Four adiabatic sidewalls, hot bottom -z, cold top +z (all no-slip)."""
+    return [(ADIABATIC, 0.0)] * 4 + [(DIRICHLET, T_bottom), (DIRICHLET, T_top)]
+
+
+def make_params(nx, ny, nz, walls, Ra=1e6, Pr=0.71, U=0.1, H=0.0, nu=None, kappa=None, gbeta=None,
+                body_force=(0.0, 0.0, 0.0), storage="fp32", streaming="aa", diag_every=0,
+                block_size=0) -> LbmParams:
+    p = LbmParams()
+    p.nx, p.ny, p.nz = int(nx), int(ny), int(nz)
+    p.Ra, p.Pr, p.U, p.H = float(Ra), float(Pr), float(U), float(H)
+    if nu is not None:
+        p.derive = 0
+        p.nu, p.kappa, p.gbeta = float(nu), float(kappa), float(gbeta)
+    else:
+        p.derive = 1
+    for a in range(3):
+        p.body_force[a] = float(body_force[a])
+    for k, (kind, tw) in enumerate(walls):
+        p.wall[k].kind = int(kind)
+        p.wall[k].T_w = float(tw)
+    p.storage = STORAGE[storage] if isinstance(storage, str) else int(storage)
+    p.streaming = STREAMING[streaming] if isinstance(streaming, str) else int(streaming)
+    p.diag_every = int(diag_every)
+    p.block_size = int(block_size)
+    return p
+
+
+# --------------------------------------------------------------- context --
+
+def _check(ctx, status, diag=None):
+    if status != LBM_OK:
+        msg = lib().lbm_last_error(ctx).decode() if ctx is not None else lib().lbm_last_error(None).decode()
+        raise LbmError(status, msg, diag)
+
+
+def lbm_create(params: LbmParams, allocator="torch", stream=None):
+    """Create a context.  allocator: "torch" (PyTorch caching allocator) or None
+    (the library calls cudaMalloc).  stream: a torch.cuda.Stream, a raw
+    cudaStream_t as int, or None for the current PyTorch stream."""
+    L = lib()
+    if allocator == "torch":
+        alloc = ctypes.byref(torch_allocator())
+    else:
+        alloc = None
+    if stream is None:
+        import torch
+
+        stream = torch.cuda.current_stream().cuda_stream
+    elif hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    ctx = ctypes.c_void_p()
+    st = L.lbm_create(ctypes.byref(params), alloc, c_void_p(int(stream) or None), ctypes.byref(ctx))
+    if st != LBM_OK:
+        raise LbmError(st, L.lbm_last_error(None).decode())
+    return ctx
+
+
+def lbm_destroy(ctx):
+    lib().lbm_destroy(ctx)
+
+
+def lbm_last_error(ctx) -> str:
+    return lib().lbm_last_error(ctx).decode()
+
+
+def lbm_get_constants(ctx) -> dict:
+    c = LbmConstants()
+    _check(ctx, lib().lbm_get_constants(ctx, ctypes.byref(c)))
+    return {k: getattr(c, k) for k, _ in c._fields_}
+
+
+def _dims(ctx):
+    c = LbmConstants()
+    lib().lbm_get_constants(ctx, ctypes.byref(c))
+    return int(c.nodes)
+
+
+def lbm_set_fields(ctx, rho, u3, T, shape):
+    """shape = (nz, ny, nx); rho and T broadcast to it, u3 to (3,) + shape."""
+    u3 = np.asarray(u3, dtype=np.float64)
+    if u3.ndim == 1:
+        u3 = u3.reshape(3, 1, 1, 1)
+    r, u, t = _f64(rho, shape), _f64(u3, (3,) + tuple(shape)), _f64(T, shape)
+    _check(ctx, lib().lbm_set_fields(ctx, _dp(r), _dp(u), _dp(t)))
+
+
+def lbm_set_populations(ctx, f19, g7):
+    f = np.ascontiguousarray(f19, dtype=np.float64)
+    g = np.ascontiguousarray(g7, dtype=np.float64)
+    n = _dims(ctx)
+    assert f.size == 19 * n and g.size == 7 * n
+    _check(ctx, lib().lbm_set_populations(ctx, _dp(f), _dp(g)))
+
+
+def lbm_get_populations(ctx, shape):
+    f = np.empty((19,) + tuple(shape))
+    g = np.empty((7,) + tuple(shape))
+    _check(ctx, lib().lbm_get_populations(ctx, _dp(f), _dp(g)))
+    return f, g
+
+
+def lbm_get_populations_at(ctx, nodes):
+    nodes = np.ascontiguousarray(nodes, dtype=np.int64)
+    f = np.empty((len(nodes), 19))
+    g = np.empty((len(nodes), 7))
+    st = lib().lbm_get_populations_at(ctx, nodes.ctypes.data_as(ctypes.POINTER(c_int64)), len(nodes), _dp(f),
+                                      _dp(g))
+    _check(ctx, st)
+    return f, g
+
+
+def lbm_step(ctx, n: int):
+    _check(ctx, lib().lbm_step(ctx, int(n)))
+
+
+def lbm_moments(ctx, shape):
+    rho = np.empty(tuple(shape))
+    u3 = np.empty((3,) + tuple(shape))
+    T = np.empty(tuple(shape))
+    _check(ctx, lib().lbm_moments(ctx, _dp(rho), _dp(u3), _dp(T)))
+    return rho, u3, T
+
+
+def lbm_sample(ctx):
+    _check(ctx, lib().lbm_sample(ctx))
+
+
+def lbm_diagnostics(ctx, reset: bool = False, raise_on_diverged: bool = True) -> dict:
+    d = LbmDiag()
+    st = lib().lbm_diagnostics(ctx, ctypes.byref(d), int(bool(reset)))
+    out = d.as_dict()
+    if st == LBM_ERR_DIVERGED and not raise_on_diverged:
+        out["diverged"] = True
+        return out
+    _check(ctx, st, out)
+    out["diverged"] = False
+    return out
+
+
+def lbm_synchronize(ctx):
+    _check(ctx, lib().lbm_synchronize(ctx))
+
+
+def lbm_save(ctx, path: str):
+    _check(ctx, lib().lbm_save(ctx, os.fsencode(path)))
+
+
+def lbm_load(ctx, path: str):
+    _check(ctx, lib().lbm_load(ctx, os.fsencode(path)))
+
+
+def lbm_device_view(ctx):
+    f, g = ctypes.c_void_p(), ctypes.c_void_p()
+    stride, eb = c_int64(), c_int()
+    _check(ctx, lib().lbm_device_view(ctx, ctypes.byref(f), ctypes.byref(g), ctypes.byref(stride),
+                                      ctypes.byref(eb)))
+    return f.value, g.value, stride.value, eb.value
+
+
+class Lattice:
+    """Owns one context; methods forward to the lbm_* functions above."""
+
+    def __init__(self, nx, ny, nz, walls, allocator="torch", stream=None, **kw):
+        self.shape = (nz, ny, nx)
+        self.params = make_params(nx, ny, nz, walls, **kw)
+        self.ctx = lbm_create(self.params, allocator=allocator, stream=stream)
+
+    def close(self):
+        if self.ctx is not None and self.ctx.value:
+            lbm_destroy(self.ctx)
+        self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    constants = property(lambda self: lbm_get_constants(self.ctx))
+
+    def set_fields(self, rho, u3, T):
+        lbm_set_fields(self.ctx, rho, u3, T, self.shape)
+
+    def set_populations(self, f, g):
+        lbm_set_populations(self.ctx, f, g)
+
+    def populations(self):
+        return lbm_get_populations(self.ctx, self.shape)
+
+    def populations_at(self, nodes):
+        return lbm_get_populations_at(self.ctx, nodes)
+
+    def step(self, n=1):
+        lbm_step(self.ctx, n)
+
+    def moments(self):
+        return lbm_moments(self.ctx, self.shape)
+
+    def sample(self):
+        lbm_sample(self.ctx)
+
+    def diagnostics(self, reset=False, raise_on_diverged=True):
+        return lbm_diagnostics(self.ctx, reset, raise_on_diverged)
+
+    def synchronize(self):
+        lbm_synchronize(self.ctx)
+
+    def save(self, path):
+        lbm_save(self.ctx, path)
+
+    def load(self, path):
+        lbm_load(self.ctx, path)
