@@ -220,6 +220,42 @@ lbm_status lbm_load(lbm_ctx *ctx, const char *path);
  * lbm_get_populations to read them in a defined layout. */
 lbm_status lbm_device_view(lbm_ctx *ctx, void **f, void **g, int64_t *stride, int *elem_bytes);
 
+/* Allocation-free diagnostics reduction.  The paper has no counterpart.
+ *
+ * Some callers cannot allocate device memory at the moment they need the
+ * global sums: an application that reserves the whole GPU for its own pool at
+ * start-up, a solver loop that must not call cudaMalloc while running (the
+ * call may synchronise the device and its latency is unbounded), or a plugin
+ * whose host framework owns every device allocation.  This entry point
+ * performs the reduction of lbm_sample / lbm_diagnostics on fields the caller
+ * already holds on the device, and allocates nothing: its per-block partial
+ * sums live in a fixed static device array of LBM_NOALLOC_MAX_BLOCKS rows of
+ * LBM_NDIAG doubles plus LBM_NDIAG + 1 accumulator slots (233,672 bytes),
+ * which every GPU that loads the library holds until the process exits.
+ *
+ *   fields  device, 11 arrays of `stride` floats, x fastest: rho - rho0, u, v,
+ *           w, T of every node, then for each face f = 0..5 the pre-collision
+ *           g arriving from that face (velocity index f + 1) at the nodes next
+ *           to it (read only where face f is a Dirichlet wall).
+ *   stride  elements between consecutive arrays, >= nx ny nz.
+ *   walls   six faces -x, +x, -y, +y, -z, +z, as in lbm_params.
+ *   a_T     the D3Q7 constant of the cell (lbm_constants.a_T), in (-6, 1).
+ *   blocks  reduction blocks, 0 for the default the contexts use; more than
+ *           LBM_NOALLOC_MAX_BLOCKS does not fit the static array and returns
+ *           LBM_ERR_PARAM.
+ *   sums    device, LBM_NDIAG doubles receiving the raw sums (lbm_diag.raw).
+ *   stream  cudaStream_t the kernels run on (NULL: legacy default stream).
+ * Asynchronous.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) and caches it; make that first call before
+ * any stream capture.  All calls share the array and it keeps the last
+ * call's contents: the accumulator slots are cleared at the start of every
+ * call, and calls that overlap on a GPU race.  Errors: LBM_ERR_PARAM for an
+ * invalid argument, LBM_ERR_CUDA for a failed launch; lbm_last_error(NULL)
+ * describes it. */
+#define LBM_NOALLOC_MAX_BLOCKS 1216
+lbm_status lbm_reduce_noalloc(const float *fields, int64_t stride, int nx, int ny, int nz,
+                              const lbm_wall *walls, double a_T, int blocks, double *sums, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -20,6 +20,11 @@ const int kMagic = 0x4c424d33; // "LBM3"
 
 } // namespace
 
+namespace lbm {
+// Message returned by lbm_last_error(NULL) after a failed context-free call.
+void set_global_error(const std::string &msg) { g_create_error = msg; }
+} // namespace lbm
+
 struct lbm_ctx {
     lbm_params p{};
     lbm_constants c{};

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "lbm_device.cuh"
 
 namespace lbm {
@@ -39,5 +41,8 @@ cudaError_t launch_equilibrium(float *st, const float *fields, uint32_t n, const
 int diag_blocks(const Geom &G);
 cudaError_t launch_diag(const float *mom, const Geom &G, const Phys &P, const float *wallT,
                         double *partial, int nblocks, double *raw, double *acc, cudaStream_t stream);
+
+// Sets the message lbm_last_error(NULL) returns.
+void set_global_error(const std::string &msg);
 
 } // namespace lbm

@@ -109,6 +109,8 @@ def lib():
         "lbm_save": ([c_void_p, ctypes.c_char_p], c_int),
         "lbm_load": ([c_void_p, ctypes.c_char_p], c_int),
         "lbm_device_view": ([c_void_p, C, C, i64p, P(c_int)], c_int),
+        "lbm_reduce_noalloc": ([c_void_p, c_int64, c_int, c_int, c_int, P(LbmWall), c_double, c_int, c_void_p,
+                                c_void_p], c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -323,6 +325,21 @@ def lbm_device_view(ctx):
     _check(ctx, lib().lbm_device_view(ctx, ctypes.byref(f), ctypes.byref(g), ctypes.byref(stride),
                                       ctypes.byref(eb)))
     return f.value, g.value, stride.value, eb.value
+
+
+def lbm_reduce_noalloc(fields_ptr: int, stride: int, nx: int, ny: int, nz: int, walls, a_T: float,
+                       sums_ptr: int, blocks: int = 0, stream=None):
+    """Allocation-free diagnostics reduction over caller-held device fields
+    (device pointers as ints; see include/lbm.h).  The paper has no
+    counterpart; it serves callers that must not allocate device memory."""
+    w = (LbmWall * 6)()
+    for k, (kind, tw) in enumerate(walls):
+        w[k].kind, w[k].T_w = int(kind), float(tw)
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    st = lib().lbm_reduce_noalloc(c_void_p(fields_ptr), int(stride), int(nx), int(ny), int(nz), w, float(a_T),
+                                  int(blocks), c_void_p(sums_ptr), c_void_p(int(stream or 0) or None))
+    _check(None, st)
 
 
 class Lattice:
