@@ -345,6 +345,7 @@ def run_gpu(args):
 
 
 def main():
+    global N_EDGE
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
@@ -352,7 +353,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp32-only", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--edge", type=int, default=N_EDGE, help="cube edge; other than 257 only for profiling")
     args = ap.parse_args()
+    N_EDGE = args.edge
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -49,59 +49,9 @@ __host__ __device__ constexpr int opp7(int i) {
     return t[i];
 }
 
-// D3Q19 transformation matrix M of Sec. 2.2 (rows: moments rho, e, eps, jx,
-// qx, jy, qy, jz, qz, 3pxx, 3pixx, pww, piww, pxy, pyz, pxz, mx, my, mz).
-__host__ __device__ constexpr int Mk(int k, int i) {
-    constexpr int t[19][19] = {
-        {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1},
-        {-30, -11, -11, -11, -11, -11, -11, 8, 8, 8, 8, 8, 8, 8, 8, 8, 8, 8, 8},
-        {12, -4, -4, -4, -4, -4, -4, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1},
-        {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0},
-        {0, -4, 4, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0},
-        {0, 0, 0, 1, -1, 0, 0, 1, 1, -1, -1, 0, 0, 0, 0, 1, -1, 1, -1},
-        {0, 0, 0, -4, 4, 0, 0, 1, 1, -1, -1, 0, 0, 0, 0, 1, -1, 1, -1},
-        {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, 1, -1, -1, 1, 1, -1, -1},
-        {0, 0, 0, 0, 0, -4, 4, 0, 0, 0, 0, 1, 1, -1, -1, 1, 1, -1, -1},
-        {0, 2, 2, -1, -1, -1, -1, 1, 1, 1, 1, 1, 1, 1, 1, -2, -2, -2, -2},
-        {0, -4, -4, 2, 2, 2, 2, 1, 1, 1, 1, 1, 1, 1, 1, -2, -2, -2, -2},
-        {0, 0, 0, 1, 1, -1, -1, 1, 1, 1, 1, -1, -1, -1, -1, 0, 0, 0, 0},
-        {0, 0, 0, -2, -2, 2, 2, 1, 1, 1, 1, -1, -1, -1, -1, 0, 0, 0, 0},
-        {0, 0, 0, 0, 0, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 0, 0, 0, 0},
-        {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1, -1, -1, 1},
-        {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0},
-        {0, 0, 0, 0, 0, 0, 0, 1, -1, 1, -1, -1, 1, -1, 1, 0, 0, 0, 0},
-        {0, 0, 0, 0, 0, 0, 0, -1, -1, 1, 1, 0, 0, 0, 0, 1, -1, 1, -1},
-        {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 1, -1, -1, -1, -1, 1, 1}};
-    return t[k][i];
-}
-// Squared row norms of M: M^-1 = M^T diag(1/|M_k|^2).
-__host__ __device__ constexpr int Mnorm(int k) {
-    constexpr int t[19] = {19, 2394, 252, 10, 40, 10, 40, 10, 40, 36, 72, 12, 24, 4, 4, 4, 8, 8, 8};
-    return t[k];
-}
-// D3Q7 transformation matrix N of Sec. 2.3 with the <e_z| row taken from its
-// definition (0, 0, 0, 0, 0, 1, -1).
-__host__ __device__ constexpr int Nk(int k, int i) {
-    constexpr int t[7][7] = {{1, 1, 1, 1, 1, 1, 1},   {0, 1, -1, 0, 0, 0, 0},
-                             {0, 0, 0, 1, -1, 0, 0},  {0, 0, 0, 0, 0, 1, -1},
-                             {-6, 1, 1, 1, 1, 1, 1},  {0, 2, 2, -1, -1, -1, -1},
-                             {0, 0, 0, 1, 1, -1, -1}};
-    return t[k][i];
-}
-__host__ __device__ constexpr int Nnorm(int k) {
-    constexpr int t[7] = {7, 2, 2, 2, 42, 12, 4};
-    return t[k];
-}
 // D3Q19 weights w_i (Sec. 2.2).
 __host__ __device__ constexpr float w19(int i) {
     return i == 0 ? 1.0f / 3.0f : (i < 7 ? 1.0f / 18.0f : 1.0f / 36.0f);
-}
-
-// Accumulate c * x for a compile-time integer coefficient c.
-__device__ __forceinline__ void acc_int(float &s, int c, float x) {
-    if (c == 1) s += x;
-    else if (c == -1) s -= x;
-    else if (c != 0) s = fmaf(static_cast<float>(c), x, s);
 }
 
 // -------------------------------------------------------- storage types ----
@@ -206,27 +156,26 @@ __host__ __device__ constexpr int face_of(int ex, int ey, int ez) {
 }
 
 // ------------------------------------------------------------- collision ----
+//
+// Opposite velocity pairs (i, ibar) in paper order: (1,2) (3,4) (5,6) (7,10)
+// (8,9) (11,14) (12,13) (15,18) (16,17) for D3Q19 and (1,2) (3,4) (5,6) for
+// D3Q7.  Every row of M and N is a polynomial that is even or odd in e, so an
+// even moment sees a pair only through s = f_i + f_ibar and an odd moment only
+// through d = f_i - f_ibar; likewise M^T splits into an even part E and an odd
+// part O with f_i+ = f_i - E - O and f_ibar+ = f_ibar - E + O.  The sums below
+// are the rows of M and N of Secs. 2.2-2.3 written over s and d.
 
-// Moments of one node: mom = (rho - rho0, u, v, w, T) with
-// u = (sum e f + F/2)/rho and F = body force + rho g beta T z-hat (Sec. 2.2).
+// Moments of one node: rho - rho0, rho, u = (sum e f + F/2)/rho, T, and the
+// force F = body force + rho g beta T z-hat (Sec. 2.2).
 struct Macro {
     float drho, rho, u, v, w, T, Fx, Fy, Fz;
 };
 
-__device__ __forceinline__ Macro macro(const Phys &P, const float (&f)[19], const float (&g)[7]) {
+__host__ __device__ __forceinline__ Macro macro_from(const Phys &P, float drho, float jx, float jy, float jz,
+                                                     float T) {
     Macro m;
-    float dr = 0.f, jx = 0.f, jy = 0.f, jz = 0.f, T = 0.f;
-#pragma unroll
-    for (int i = 0; i < 19; ++i) {
-        dr += f[i];
-        acc_int(jx, ex19(i), f[i]);
-        acc_int(jy, ey19(i), f[i]);
-        acc_int(jz, ez19(i), f[i]);
-    }
-#pragma unroll
-    for (int i = 0; i < 7; ++i) T += g[i];
-    const float rho = 1.0f + dr;
-    m.drho = dr;
+    const float rho = 1.0f + drho;
+    m.drho = drho;
     m.rho = rho;
     m.T = T;
     m.Fx = P.bf[0];
@@ -239,100 +188,131 @@ __device__ __forceinline__ Macro macro(const Phys &P, const float (&f)[19], cons
     return m;
 }
 
+__host__ __device__ __forceinline__ Macro macro(const Phys &P, const float (&f)[19], const float (&g)[7]) {
+    const float dr = f[0] + ((f[1] + f[2]) + (f[3] + f[4]) + (f[5] + f[6])) +
+                     (((f[7] + f[10]) + (f[8] + f[9])) + ((f[11] + f[14]) + (f[12] + f[13])) +
+                      ((f[15] + f[18]) + (f[16] + f[17])));
+    const float jx = (f[1] - f[2]) + ((f[7] - f[10]) - (f[8] - f[9])) + ((f[11] - f[14]) - (f[12] - f[13]));
+    const float jy = (f[3] - f[4]) + ((f[7] - f[10]) + (f[8] - f[9])) + ((f[15] - f[18]) - (f[16] - f[17]));
+    const float jz = (f[5] - f[6]) + ((f[11] - f[14]) + (f[12] - f[13])) + ((f[15] - f[18]) + (f[16] - f[17]));
+    const float T = g[0] + (g[1] + g[2]) + (g[3] + g[4]) + (g[5] + g[6]);
+    return macro_from(P, dr, jx, jy, jz, T);
+}
+
 // One fused collision of both distributions at one node, in place:
 //   f+ = f - M^-1 [S (m - m^eq) - (I - S/2) M F~]      (Eq. MRT)
 //   g+ = g - N^-1 Q (n - n^eq)                          (Eq. MRT_T)
 // f holds deviations f - w rho0; the rest-state moments M w rho0 =
 // (rho0, -11 rho0, 3 rho0, 0, ...) are folded into m - m^eq below.
-__device__ __forceinline__ Macro collide(const Phys &P, float (&f)[19], float (&g)[7]) {
-    const Macro mc = macro(P, f, g);
-    const float rho = mc.rho, u = mc.u, v = mc.v, w = mc.w, T = mc.T;
+// M^-1 = M^T diag(1/|M_k|^2), N^-1 = N^T diag(1/|N_k|^2).
+__host__ __device__ __forceinline__ Macro collide(const Phys &P, float (&f)[19], float (&g)[7]) {
+    constexpr int I[9] = {1, 3, 5, 7, 8, 11, 12, 15, 16};
+    constexpr int J[9] = {2, 4, 6, 10, 9, 14, 13, 18, 17};
+    float s[9], d[9];
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+        s[p] = f[I[p]] + f[J[p]];
+        d[p] = f[I[p]] - f[J[p]];
+    }
+    const float f0 = f[0];
+    const float s34 = s[3] + s[4], s56 = s[5] + s[6], s78 = s[7] + s[8];
+    const float Sax = (s[0] + s[1]) + s[2];
+    const float Sdg = (s34 + s56) + s78;
+    const float dx = (d[3] - d[4]) + (d[5] - d[6]); // diagonal parts of j
+    const float dy = (d[3] + d[4]) + (d[7] - d[8]);
+    const float dz = (d[5] + d[6]) + (d[7] + d[8]);
+    const float gs0 = g[1] + g[2], gs1 = g[3] + g[4], gs2 = g[5] + g[6];
+    const float T = g[0] + (gs0 + gs1) + gs2;
+    const Macro mc = macro_from(P, f0 + Sax + Sdg, d[0] + dx, d[1] + dy, d[2] + dz, T);
+    const float rho = mc.rho, u = mc.u, v = mc.v, w = mc.w;
     const float Fx = mc.Fx, Fy = mc.Fy, Fz = mc.Fz;
 
-    // non-conserved moments of the deviations
-    float m[19];
-#pragma unroll
-    for (int k = 0; k < 19; ++k) {
-        m[k] = 0.f;
-        if (k == 0 || k == 3 || k == 5 || k == 7) continue;
-#pragma unroll
-        for (int i = 0; i < 19; ++i) acc_int(m[k], Mk(k, i), f[i]);
-    }
+    // m - m^eq (Sec. 2.2 m^eq) of the non-conserved moments
     const float uu = u * u + v * v + w * w;
     const float ru = rho * u, rv = rho * v, rw = rho * w;
     const float pxx = rho * (2.f * u * u - v * v - w * w);
     const float pww = rho * (v * v - w * w);
-    // m - m^eq in deviation form (Sec. 2.2 m^eq)
-    float d[19];
-    d[1] = m[1] + 11.f * mc.drho - 19.f * rho * uu;
-    d[2] = m[2] - 3.f * mc.drho + 5.5f * rho * uu;
-    d[4] = m[4] + (2.f / 3.f) * ru;
-    d[6] = m[6] + (2.f / 3.f) * rv;
-    d[8] = m[8] + (2.f / 3.f) * rw;
-    d[9] = m[9] - pxx;
-    d[10] = m[10] + 0.5f * pxx;
-    d[11] = m[11] - pww;
-    d[12] = m[12] + 0.5f * pww;
-    d[13] = m[13] - ru * v;
-    d[14] = m[14] - rv * w;
-    d[15] = m[15] - ru * w;
-    d[16] = m[16];
-    d[17] = m[17];
-    d[18] = m[18];
-    // forcing moments M F~ (Sec. 2.2)
+    const float s3456 = s34 + s56;
+    const float d1 = (-30.f * f0 - 11.f * Sax + 8.f * Sdg) + 11.f * mc.drho - 19.f * rho * uu;
+    const float d2 = (12.f * f0 - 4.f * Sax + Sdg) - 3.f * mc.drho + 5.5f * rho * uu;
+    const float d4 = (-4.f * d[0] + dx) + (2.f / 3.f) * ru;
+    const float d6 = (-4.f * d[1] + dy) + (2.f / 3.f) * rv;
+    const float d8 = (-4.f * d[2] + dz) + (2.f / 3.f) * rw;
+    const float d9 = (2.f * s[0] - s[1] - s[2] + s3456 - 2.f * s78) - pxx;
+    const float d10 = (-4.f * s[0] + 2.f * s[1] + 2.f * s[2] + s3456 - 2.f * s78) + 0.5f * pxx;
+    const float d11 = (s[1] - s[2] + s34 - s56) - pww;
+    const float d12 = (-2.f * s[1] + 2.f * s[2] + s34 - s56) + 0.5f * pww;
+    const float d13 = (s[3] - s[4]) - ru * v;
+    const float d14 = (s[7] - s[8]) - rv * w;
+    const float d15 = (s[5] - s[6]) - ru * w;
+    const float d16 = (d[3] - d[4]) - (d[5] - d[6]);
+    const float d17 = (d[7] - d[8]) - (d[3] + d[4]);
+    const float d18 = (d[5] + d[6]) - (d[7] + d[8]);
+
+    // a_k, b_k = [S (m - m^eq) - (I - S/2) M F~]_k / |M_k|^2 (even k: a, odd k: b)
     const float uF = u * Fx + v * Fy + w * Fz;
-    const float ce = 1.f - 0.5f * P.s_e, cq = 1.f - 0.5f * P.s_q;
-    float D[19]; // S (m - m^eq) - (I - S/2) M F~, divided by |M_k|^2
-    D[0] = 0.f;
-    D[1] = (P.s_e * d[1] - ce * 38.f * uF) * (1.f / Mnorm(1));
-    D[2] = (P.s_e * d[2] + ce * 11.f * uF) * (1.f / Mnorm(2));
-    D[3] = -Fx * (1.f / Mnorm(3));
-    D[4] = (P.s_q * d[4] + cq * (2.f / 3.f) * Fx) * (1.f / Mnorm(4));
-    D[5] = -Fy * (1.f / Mnorm(5));
-    D[6] = (P.s_q * d[6] + cq * (2.f / 3.f) * Fy) * (1.f / Mnorm(6));
-    D[7] = -Fz * (1.f / Mnorm(7));
-    D[8] = (P.s_q * d[8] + cq * (2.f / 3.f) * Fz) * (1.f / Mnorm(8));
-    D[9] = (P.s_e * d[9] - ce * (4.f * u * Fx - 2.f * v * Fy - 2.f * w * Fz)) * (1.f / Mnorm(9));
-    D[10] = (P.s_e * d[10] - ce * (-2.f * u * Fx + v * Fy + w * Fz)) * (1.f / Mnorm(10));
-    D[11] = (P.s_e * d[11] - ce * (2.f * v * Fy - 2.f * w * Fz)) * (1.f / Mnorm(11));
-    D[12] = (P.s_e * d[12] - ce * (-v * Fy + w * Fz)) * (1.f / Mnorm(12));
-    D[13] = (P.s_e * d[13] - ce * (u * Fy + v * Fx)) * (1.f / Mnorm(13));
-    D[14] = (P.s_e * d[14] - ce * (v * Fz + w * Fy)) * (1.f / Mnorm(14));
-    D[15] = (P.s_e * d[15] - ce * (u * Fz + w * Fx)) * (1.f / Mnorm(15));
-    D[16] = P.s_q * d[16] * (1.f / Mnorm(16));
-    D[17] = P.s_q * d[17] * (1.f / Mnorm(17));
-    D[18] = P.s_q * d[18] * (1.f / Mnorm(18));
+    const float se = P.s_e, sq = P.s_q;
+    const float ce = 1.f - 0.5f * se, cq = 1.f - 0.5f * sq;
+    const float a1 = (se * d1 - ce * 38.f * uF) * (1.f / 2394.f);
+    const float a2 = (se * d2 + ce * 11.f * uF) * (1.f / 252.f);
+    const float a9 = (se * d9 - ce * (4.f * u * Fx - 2.f * v * Fy - 2.f * w * Fz)) * (1.f / 36.f);
+    const float a10 = (se * d10 - ce * (-2.f * u * Fx + v * Fy + w * Fz)) * (1.f / 72.f);
+    const float a11 = (se * d11 - ce * (2.f * v * Fy - 2.f * w * Fz)) * (1.f / 12.f);
+    const float a12 = (se * d12 - ce * (-v * Fy + w * Fz)) * (1.f / 24.f);
+    const float a13 = (se * d13 - ce * (u * Fy + v * Fx)) * 0.25f;
+    const float a14 = (se * d14 - ce * (v * Fz + w * Fy)) * 0.25f;
+    const float a15 = (se * d15 - ce * (u * Fz + w * Fx)) * 0.25f;
+    const float b3 = -Fx * 0.1f, b5 = -Fy * 0.1f, b7 = -Fz * 0.1f;
+    const float b4 = (sq * d4 + cq * (2.f / 3.f) * Fx) * (1.f / 40.f);
+    const float b6 = (sq * d6 + cq * (2.f / 3.f) * Fy) * (1.f / 40.f);
+    const float b8 = (sq * d8 + cq * (2.f / 3.f) * Fz) * (1.f / 40.f);
+    const float b16 = sq * d16 * 0.125f, b17 = sq * d17 * 0.125f, b18 = sq * d18 * 0.125f;
+
+    // M^T applied to (a, b): even parts E_p and odd parts O_p of each pair
+    const float Cax = -11.f * a1 - 4.f * a2, Cdg = 8.f * a1 + a2;
+    const float X = a9 + a10, Y = a11 + a12, Z = a11 - 2.f * a12;
+    const float Jx = b3 + b4, Jy = b5 + b6, Jz = b7 + b8;
+    float E[9], O[9];
+    E[0] = Cax + 2.f * a9 - 4.f * a10;
+    E[1] = Cax - a9 + 2.f * a10 + Z;
+    E[2] = Cax - a9 + 2.f * a10 - Z;
+    E[3] = Cdg + X + Y + a13;
+    E[4] = Cdg + X + Y - a13;
+    E[5] = Cdg + X - Y + a15;
+    E[6] = Cdg + X - Y - a15;
+    E[7] = Cdg - 2.f * X + a14;
+    E[8] = Cdg - 2.f * X - a14;
+    O[0] = b3 - 4.f * b4;
+    O[1] = b5 - 4.f * b6;
+    O[2] = b7 - 4.f * b8;
+    O[3] = Jx + Jy + (b16 - b17);
+    O[4] = -Jx + Jy - (b16 + b17);
+    O[5] = Jx + Jz + (b18 - b16);
+    O[6] = -Jx + Jz + (b16 + b18);
+    O[7] = Jy + Jz + (b17 - b18);
+    O[8] = -Jy + Jz - (b17 + b18);
+    f[0] = f0 - (-30.f * a1 + 12.f * a2);
 #pragma unroll
-    for (int i = 0; i < 19; ++i) {
-        float c = 0.f;
-#pragma unroll
-        for (int k = 1; k < 19; ++k) acc_int(c, Mk(k, i), D[k]);
-        f[i] -= c;
+    for (int p = 0; p < 9; ++p) {
+        f[I[p]] -= E[p] + O[p];
+        f[J[p]] -= E[p] - O[p];
     }
 
-    // D3Q7: n - n^eq with n^eq = (T, uT, vT, wT, a_T T, 0, 0)
-    float n[7];
-#pragma unroll
-    for (int k = 1; k < 7; ++k) {
-        n[k] = 0.f;
-#pragma unroll
-        for (int i = 0; i < 7; ++i) acc_int(n[k], Nk(k, i), g[i]);
-    }
-    float E[7];
-    E[0] = 0.f;
-    E[1] = P.q_k * (n[1] - u * T) * (1.f / Nnorm(1));
-    E[2] = P.q_k * (n[2] - v * T) * (1.f / Nnorm(2));
-    E[3] = P.q_k * (n[3] - w * T) * (1.f / Nnorm(3));
-    E[4] = P.q_e * (n[4] - P.a_T * T) * (1.f / Nnorm(4));
-    E[5] = P.q_e * n[5] * (1.f / Nnorm(5));
-    E[6] = P.q_e * n[6] * (1.f / Nnorm(6));
-#pragma unroll
-    for (int i = 0; i < 7; ++i) {
-        float c = 0.f;
-#pragma unroll
-        for (int k = 1; k < 7; ++k) acc_int(c, Nk(k, i), E[k]);
-        g[i] -= c;
-    }
+    // D3Q7: n - n^eq with n^eq = (T, uT, vT, wT, a_T T, 0, 0); |N_k|^2 = 7, 2, 2, 2, 42, 12, 4
+    const float e1 = P.q_k * ((g[1] - g[2]) - u * T) * 0.5f;
+    const float e2 = P.q_k * ((g[3] - g[4]) - v * T) * 0.5f;
+    const float e3 = P.q_k * ((g[5] - g[6]) - w * T) * 0.5f;
+    const float e4 = P.q_e * ((-6.f * g[0] + (gs0 + gs1) + gs2) - P.a_T * T) * (1.f / 42.f);
+    const float e5 = P.q_e * (2.f * gs0 - gs1 - gs2) * (1.f / 12.f);
+    const float e6 = P.q_e * (gs1 - gs2) * 0.25f;
+    g[0] += 6.f * e4;
+    const float E1 = e4 + 2.f * e5, E2 = e4 - e5 + e6, E3 = e4 - e5 - e6;
+    g[1] -= E1 + e1;
+    g[2] -= E1 - e1;
+    g[3] -= E2 + e2;
+    g[4] -= E2 - e2;
+    g[5] -= E3 + e3;
+    g[6] -= E3 - e3;
     return mc;
 }
 

@@ -27,6 +27,14 @@ enum Layout { LAYOUT_NATURAL = 0, LAYOUT_REVERSED = 1, LAYOUT_PULL = 2 };
 
 template <int S> using SE = typename Store<S>::T;
 
+// Hide a pointer's value from the compiler so that addresses computed from it
+// before the collision are not kept live across it (recomputing 26 addresses
+// costs a few instructions; keeping them costs 52 registers).
+template <typename T> __device__ __forceinline__ T *opaque(T *p) {
+    asm volatile("" : "+l"(p));
+    return p;
+}
+
 // Read the pre-collision populations of node (x, y, z) from a device layout.
 template <int S>
 __device__ __forceinline__ void read_natural(const SE<S> *__restrict__ f, const SE<S> *__restrict__ g,
@@ -85,7 +93,7 @@ __device__ __forceinline__ void write_sample(float *__restrict__ mom, int64_t s,
 
 // Even step: natural -> reversed.  Reads and writes only the node's own slots.
 template <int S, bool MOM>
-__global__ void __launch_bounds__(256) k_aa_even(SE<S> *__restrict__ f, SE<S> *__restrict__ g, Geom G,
+__global__ void __launch_bounds__(256, 3) k_aa_even(SE<S> *__restrict__ f, SE<S> *__restrict__ g, Geom G,
                                                  Phys P, float *__restrict__ mom) {
     const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= G.n) return;
@@ -99,6 +107,8 @@ __global__ void __launch_bounds__(256) k_aa_even(SE<S> *__restrict__ f, SE<S> *_
 #pragma unroll
     for (int i = 0; i < 7; ++i) g0[i] = gl[i];
     const Macro m = collide(P, fl, gl);
+    f = opaque(f);
+    g = opaque(g);
 #pragma unroll
     for (int i = 0; i < 19; ++i) Store<S>::st(f + opp19(i) * s + n, fl[i]);
 #pragma unroll
@@ -115,7 +125,7 @@ __global__ void __launch_bounds__(256) k_aa_even(SE<S> *__restrict__ f, SE<S> *_
 // location a thread reads is written by that same thread only, so the update
 // is in place without a second buffer.
 template <int S, bool MOM>
-__global__ void __launch_bounds__(256) k_aa_odd(SE<S> *__restrict__ f, SE<S> *__restrict__ g, Geom G,
+__global__ void __launch_bounds__(256, 3) k_aa_odd(SE<S> *__restrict__ f, SE<S> *__restrict__ g, Geom G,
                                                 Phys P, float *__restrict__ mom) {
     const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= G.n) return;
@@ -145,6 +155,8 @@ __global__ void __launch_bounds__(256) k_aa_odd(SE<S> *__restrict__ f, SE<S> *__
 #pragma unroll
     for (int i = 0; i < 7; ++i) g0[i] = gl[i];
     const Macro m = collide(P, fl, gl);
+    f = opaque(f);
+    g = opaque(g);
 #pragma unroll
     for (int i = 0; i < 19; ++i) {
         if (!dst_wall(b, ex19(i), ey19(i), ez19(i)))
@@ -168,7 +180,7 @@ __global__ void __launch_bounds__(256) k_aa_odd(SE<S> *__restrict__ f, SE<S> *__
 // ------------------------------------------------------ two-buffer pull ----
 
 template <int S, bool MOM>
-__global__ void __launch_bounds__(256) k_pull(const SE<S> *__restrict__ fs, const SE<S> *__restrict__ gs,
+__global__ void __launch_bounds__(256, 3) k_pull(const SE<S> *__restrict__ fs, const SE<S> *__restrict__ gs,
                                               SE<S> *__restrict__ fd, SE<S> *__restrict__ gd, Geom G,
                                               Phys P, float *__restrict__ mom) {
     const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
