@@ -41,6 +41,9 @@ struct lbm_ctx {
     size_t mom_bytes = 0;
     double *dsum = nullptr;               // partial[nblocks][kNDiag], raw[kNDiag], acc[kNDiag + 1]
     size_t dsum_bytes = 0;
+    uint32_t *face = nullptr;             // flat indices of the nodes next to a face (AA odd step)
+    size_t face_bytes = 0;
+    uint32_t nface = 0;
     int nblocks = 0;
     int elem = 4;
     int parity = 0;        // AA: 0 natural (next step even), 1 reversed
@@ -209,7 +212,8 @@ lbm_status validate_and_derive(const lbm_params &p, lbm_constants &c, std::strin
     return LBM_OK;
 }
 
-uint64_t magic_of(uint32_t d) { return UINT64_MAX / d + 1; }
+// ceil(2^64 / d) for fast_div; d = 1 is encoded as 0.
+uint64_t magic_of(uint32_t d) { return d <= 1 ? 0 : UINT64_MAX / d + 1; }
 
 void finalize(const lbm_ctx *ctx, const double *r, double &E, double &rms_drho, double &rms_div,
               double &Re, double &Rew, double &Nuv, double &Nuk, double &Nut, double *Nuf,
@@ -239,6 +243,8 @@ lbm_status release(lbm_ctx *ctx) {
     ctx->dfree(ctx->pop2, ctx->pop_bytes);
     ctx->dfree(ctx->mom, ctx->mom_bytes);
     ctx->dfree(ctx->dsum, ctx->dsum_bytes);
+    ctx->dfree(ctx->face, ctx->face_bytes);
+    ctx->face = nullptr;
     ctx->pop = ctx->pop2 = nullptr;
     ctx->mom = nullptr;
     ctx->dsum = nullptr;
@@ -311,6 +317,17 @@ lbm_status lbm_create(const lbm_params *params, const lbm_allocator *alloc, void
     G.periodic = 0;
     for (int a = 0; a < 3; ++a)
         if (params->wall[2 * a].kind == LBM_WALL_PERIODIC) G.periodic |= 1 << a;
+    G.nix = (uint32_t)(params->nx - 2);
+    G.nixy = G.nix * (uint32_t)(params->ny - 2);
+    G.ni = G.nixy * (uint32_t)(params->nz - 2);
+    G.mag_nix = magic_of(G.nix);
+    G.mag_nixy = magic_of(G.nixy);
+    {
+        const int ex[19] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+        const int ey[19] = {0, 0, 0, 1, -1, 0, 0, 1, 1, -1, -1, 0, 0, 0, 0, 1, -1, 1, -1};
+        const int ez[19] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, 1, -1, -1, 1, 1, -1, -1};
+        for (int i = 0; i < 19; ++i) G.off[i] = ex[i] + params->nx * ey[i] + (int)G.nxy * ez[i];
+    }
 
     Phys &P = ctx->P;
     P.s_e = (float)c.s_e;
@@ -332,21 +349,35 @@ lbm_status lbm_create(const lbm_params *params, const lbm_allocator *alloc, void
     ctx->mom_bytes = (size_t)kMomArrays * G.stride * sizeof(float);
     ctx->nblocks = diag_blocks(G);
     ctx->dsum_bytes = ((size_t)ctx->nblocks * kNDiag + 2 * kNDiag + 1) * sizeof(double);
+    // nodes next to a face: the general-path share of the AA odd step
+    std::vector<uint32_t> face;
+    face.reserve((size_t)(c.nodes - G.ni));
+    for (int z = 0; z < G.nz; ++z)
+        for (int y = 0; y < G.ny; ++y)
+            for (int x = 0; x < G.nx; ++x)
+                if (x == 0 || y == 0 || z == 0 || x == G.nx - 1 || y == G.ny - 1 || z == G.nz - 1)
+                    face.push_back((uint32_t)x + (uint32_t)G.nx * ((uint32_t)y + (uint32_t)G.ny * (uint32_t)z));
+    ctx->nface = (uint32_t)face.size();
+    ctx->face_bytes = face.size() * sizeof(uint32_t);
+    ctx->face = (uint32_t *)ctx->dalloc(ctx->face_bytes);
     ctx->pop = ctx->dalloc(ctx->pop_bytes);
     if (params->streaming == LBM_STREAM_PULL2) ctx->pop2 = ctx->dalloc(ctx->pop_bytes);
     ctx->mom = (float *)ctx->dalloc(ctx->mom_bytes);
     ctx->dsum = (double *)ctx->dalloc(ctx->dsum_bytes);
-    if (!ctx->pop || !ctx->mom || !ctx->dsum || (params->streaming == LBM_STREAM_PULL2 && !ctx->pop2)) {
+    if (!ctx->pop || !ctx->mom || !ctx->dsum || !ctx->face || (params->streaming == LBM_STREAM_PULL2 && !ctx->pop2)) {
         release(ctx);
         delete ctx;
         return fail(nullptr, LBM_ERR_OOM, "device allocation failed");
     }
-    ctx->c.device_bytes = (int64_t)(ctx->pop_bytes * (ctx->pop2 ? 2 : 1) + ctx->mom_bytes + ctx->dsum_bytes);
+    ctx->c.device_bytes =
+        (int64_t)(ctx->pop_bytes * (ctx->pop2 ? 2 : 1) + ctx->mom_bytes + ctx->dsum_bytes + ctx->face_bytes);
     // rest state: all deviations zero (f = w rho0, g = 0); pad entries zero too
     cudaError_t e = cudaMemsetAsync(ctx->pop, 0, ctx->pop_bytes, ctx->stream);
     if (e == cudaSuccess && ctx->pop2) e = cudaMemsetAsync(ctx->pop2, 0, ctx->pop_bytes, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->mom, 0, ctx->mom_bytes, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->dsum, 0, ctx->dsum_bytes, ctx->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ctx->face, face.data(), ctx->face_bytes, cudaMemcpyHostToDevice, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) {
         release(ctx);
@@ -487,6 +518,8 @@ lbm_status lbm_step(lbm_ctx *ctx, int64_t nsteps) {
     a.block = ctx->block;
     a.G = ctx->G;
     a.P = ctx->P;
+    a.face = ctx->face;
+    a.nface = ctx->nface;
     a.stream = ctx->stream;
     for (int64_t t = 0; t < nsteps; ++t) {
         const bool sample = ctx->p.diag_every > 0 && ctx->step % ctx->p.diag_every == 0;

@@ -85,6 +85,11 @@ struct Geom {
     int64_t stride;
     uint64_t mag_nx, mag_nxy; // ceil(2^64 / d): exact quotients for 32-bit numerators
     int periodic;             // bit a: axis a wraps
+    // interior nodes (1 <= x <= nx-2, ...; no neighbour behind a face): count,
+    // row length nx-2 and plane size (nx-2)(ny-2) with their division magics
+    uint32_t ni, nix, nixy;
+    uint64_t mag_nix, mag_nixy;
+    int off[19]; // flat offset of e_i: ex + nx ey + nx ny ez
 };
 
 // Physical constants of one cell (FP32).
@@ -98,8 +103,11 @@ struct Phys {
     int dir_mask;    // bit f: face f is a Dirichlet wall
 };
 
+// a / d for 32-bit a and d, given mag = ceil(2^64 / d) (exact: the rounding
+// error a (mag - 2^64/d) / 2^64 stays below 2^-32 <= 1/d); d = 1 has no
+// 64-bit magic and is passed as mag = 0.
 __device__ __forceinline__ uint32_t fast_div(uint32_t a, uint64_t mag) {
-    return static_cast<uint32_t>(__umul64hi(static_cast<uint64_t>(a), mag));
+    return mag ? static_cast<uint32_t>(__umul64hi(static_cast<uint64_t>(a), mag)) : a;
 }
 
 // Offsets to the neighbours along each axis and which sides are walls.

@@ -23,6 +23,8 @@ struct StepArgs {
     Geom G;
     Phys P;
     float *mom;   // non-null: also write the node moments of the pre-step state
+    const uint32_t *face; // AA odd step: flat indices of the nodes next to a face
+    uint32_t nface;
     cudaStream_t stream;
 };
 

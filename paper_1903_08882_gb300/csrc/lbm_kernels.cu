@@ -123,12 +123,54 @@ __global__ void __launch_bounds__(256, 3) k_aa_even(SE<S> *__restrict__ f, SE<S>
 // Odd step: reversed -> natural.  Gathers f_i+(x - e_i) from the opposite
 // slot of the upstream node and scatters f_i+(x) to slot i of x + e_i; every
 // location a thread reads is written by that same thread only, so the update
-// is in place without a second buffer.
+// is in place without a second buffer, and any partition of the nodes into
+// separately launched sets is valid.  Interior nodes (no face next to them)
+// take the uniform offsets e_i of the flat index; nodes next to a face go
+// through the general path with wrap-around and wall rules.
 template <int S, bool MOM>
-__global__ void __launch_bounds__(256, 3) k_aa_odd(SE<S> *__restrict__ f, SE<S> *__restrict__ g, Geom G,
-                                                Phys P, float *__restrict__ mom) {
-    const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= G.n) return;
+__global__ void __launch_bounds__(256, 3) k_aa_odd_interior(SE<S> *__restrict__ f, SE<S> *__restrict__ g,
+                                                            Geom G, Phys P, float *__restrict__ mom) {
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= G.ni) return;
+    const uint32_t zi = fast_div(t, G.mag_nixy);
+    const uint32_t r = t - zi * G.nixy;
+    const uint32_t yi = fast_div(r, G.mag_nix);
+    const uint32_t xi = r - yi * G.nix;
+    const uint32_t n = (xi + 1) + static_cast<uint32_t>(G.nx) * ((yi + 1) + static_cast<uint32_t>(G.ny) * (zi + 1));
+    const int64_t s = G.stride;
+    float fl[19], gl[7];
+    fl[0] = Store<S>::ld(f + n);
+#pragma unroll
+    for (int i = 1; i < 19; ++i) fl[i] = Store<S>::ld(f + opp19(i) * s + (int64_t)(n - G.off[i]));
+    gl[0] = Store<S>::ld(g + n);
+#pragma unroll
+    for (int i = 1; i < 7; ++i) gl[i] = Store<S>::ld(g + opp7(i) * s + (int64_t)(n - G.off[i]));
+    const Macro m = collide(P, fl, gl);
+    f = opaque(f);
+    g = opaque(g);
+    Store<S>::st(f + n, fl[0]);
+#pragma unroll
+    for (int i = 1; i < 19; ++i) Store<S>::st(f + i * s + (int64_t)(n + G.off[i]), fl[i]);
+    Store<S>::st(g + n, gl[0]);
+#pragma unroll
+    for (int i = 1; i < 7; ++i) Store<S>::st(g + i * s + (int64_t)(n + G.off[i]), gl[i]);
+    if (MOM) {
+        mom[n] = m.drho;
+        mom[s + n] = m.u;
+        mom[2 * s + n] = m.v;
+        mom[3 * s + n] = m.w;
+        mom[4 * s + n] = m.T;
+    }
+}
+
+// Nodes next to a face, listed in `list`.
+template <int S, bool MOM>
+__global__ void __launch_bounds__(256, 3) k_aa_odd_face(SE<S> *__restrict__ f, SE<S> *__restrict__ g, Geom G,
+                                                        Phys P, float *__restrict__ mom,
+                                                        const uint32_t *__restrict__ list, uint32_t count) {
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= count) return;
+    const uint32_t n = list[t];
     const int64_t s = G.stride;
     int x, y, z;
     node_xyz(G, n, x, y, z);
@@ -329,8 +371,15 @@ static cudaError_t step_t(const StepArgs &a) {
             if (a.mom) k_aa_even<S, true><<<nb, a.block, 0, a.stream>>>(f, g, a.G, a.P, a.mom);
             else k_aa_even<S, false><<<nb, a.block, 0, a.stream>>>(f, g, a.G, a.P, nullptr);
         } else {
-            if (a.mom) k_aa_odd<S, true><<<nb, a.block, 0, a.stream>>>(f, g, a.G, a.P, a.mom);
-            else k_aa_odd<S, false><<<nb, a.block, 0, a.stream>>>(f, g, a.G, a.P, nullptr);
+            const unsigned ni = blocks_for(a.G.ni, a.block), nf = blocks_for(a.nface, a.block);
+            if (a.mom) {
+                if (ni) k_aa_odd_interior<S, true><<<ni, a.block, 0, a.stream>>>(f, g, a.G, a.P, a.mom);
+                if (nf) k_aa_odd_face<S, true><<<nf, a.block, 0, a.stream>>>(f, g, a.G, a.P, a.mom, a.face, a.nface);
+            } else {
+                if (ni) k_aa_odd_interior<S, false><<<ni, a.block, 0, a.stream>>>(f, g, a.G, a.P, nullptr);
+                if (nf)
+                    k_aa_odd_face<S, false><<<nf, a.block, 0, a.stream>>>(f, g, a.G, a.P, nullptr, a.face, a.nface);
+            }
         }
     } else {
         auto f2 = static_cast<SE<S> *>(a.f2), g2 = static_cast<SE<S> *>(a.g2);
