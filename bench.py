@@ -233,7 +233,7 @@ def bench_storage(lbm, storage, args, stream, dist, with_e2e):
     N = N_EDGE
     nodes = N ** 3
     lat = lbm.Lattice(N, N, N, lbm.walls_side_heated(), Ra=RA, Pr=PR, U=U, storage=storage,
-                      diag_every=CHUNK, stream=stream)
+                      diag_every=CHUNK, stream=stream, nodes_per_thread=args.npt)
     res = {}
     try:
         for _ in range(args.warmup):
@@ -354,6 +354,7 @@ def main():
     ap.add_argument("--fp32-only", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--edge", type=int, default=N_EDGE, help="cube edge; other than 257 only for profiling")
+    ap.add_argument("--npt", type=int, default=0, help="nodes per thread of the AA kernels (0: library default)")
     args = ap.parse_args()
     N_EDGE = args.edge
     if args.impl == "reference":

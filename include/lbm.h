@@ -91,6 +91,7 @@ typedef struct {
     int streaming;  /* lbm_streaming */
     int diag_every; /* lbm_step samples the diagnostics every diag_every steps (0: never) */
     int block_size; /* threads per block of the step kernels, 0 = library default */
+    int nodes_per_thread; /* AA step kernels: 1, or 2 (packed FP32 arithmetic); 0 = library default (2) */
 } lbm_params;
 
 /* Device memory provider.  alloc returns device memory of at least `bytes`

@@ -158,6 +158,10 @@ lbm_status validate_and_derive(const lbm_params &p, lbm_constants &c, std::strin
         why = "block_size must be 0 or a multiple of 32 in [32, 256]";
         return LBM_ERR_PARAM;
     }
+    if (p.nodes_per_thread < 0 || p.nodes_per_thread > 2) {
+        why = "nodes_per_thread must be 0, 1 or 2";
+        return LBM_ERR_PARAM;
+    }
     if (p.diag_every < 0) {
         why = "diag_every must be >= 0";
         return LBM_ERR_PARAM;
@@ -516,6 +520,7 @@ lbm_status lbm_step(lbm_ctx *ctx, int64_t nsteps) {
     a.storage = ctx->p.storage;
     a.scheme = ctx->p.streaming == LBM_STREAM_PULL2 ? 1 : 0;
     a.block = ctx->block;
+    a.wide = ctx->p.nodes_per_thread != 1;
     a.G = ctx->G;
     a.P = ctx->P;
     a.face = ctx->face;

@@ -75,6 +75,29 @@ template <> struct Store<ST_BF16> {
     static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
 };
 
+// Two consecutive elements (first index even, so 4- or 8-byte aligned).
+template <int S> struct Store2;
+template <> struct Store2<ST_F32> {
+    static __device__ __forceinline__ float2 ld(const float *p) { return *reinterpret_cast<const float2 *>(p); }
+    static __device__ __forceinline__ void st(float *p, float2 v) { *reinterpret_cast<float2 *>(p) = v; }
+};
+template <> struct Store2<ST_F16> {
+    static __device__ __forceinline__ float2 ld(const __half *p) {
+        return __half22float2(*reinterpret_cast<const __half2 *>(p));
+    }
+    static __device__ __forceinline__ void st(__half *p, float2 v) {
+        *reinterpret_cast<__half2 *>(p) = __float22half2_rn(v);
+    }
+};
+template <> struct Store2<ST_BF16> {
+    static __device__ __forceinline__ float2 ld(const __nv_bfloat16 *p) {
+        return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p));
+    }
+    static __device__ __forceinline__ void st(__nv_bfloat16 *p, float2 v) {
+        *reinterpret_cast<__nv_bfloat162 *>(p) = __float22bfloat162_rn(v);
+    }
+};
+
 // ------------------------------------------------------ kernel arguments ----
 
 // Lattice geometry.  Node index n = x + nx (y + ny z) < 2^32; population q of
@@ -173,148 +196,222 @@ __host__ __device__ constexpr int face_of(int ex, int ey, int ez) {
 // part O with f_i+ = f_i - E - O and f_ibar+ = f_ibar - E + O.  The sums below
 // are the rows of M and N of Secs. 2.2-2.3 written over s and d.
 
+// ------------------------------------------------------ vector arithmetic ----
+//
+// The collision is written once for a value type V: float (one node per
+// thread) or float2 (two nodes per thread, evaluated with the packed FP32
+// instructions of sm_100 and later: one instruction updates both nodes).
+
+__host__ __device__ __forceinline__ float2 operator+(float2 a, float2 b) {
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+    return __fadd2_rn(a, b);
+#else
+    return make_float2(a.x + b.x, a.y + b.y);
+#endif
+}
+__host__ __device__ __forceinline__ float2 operator-(float2 a) { return make_float2(-a.x, -a.y); }
+__host__ __device__ __forceinline__ float2 operator-(float2 a, float2 b) {
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+    return __fadd2_rn(a, -b);
+#else
+    return make_float2(a.x - b.x, a.y - b.y);
+#endif
+}
+__host__ __device__ __forceinline__ float2 operator*(float2 a, float2 b) {
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+    return __fmul2_rn(a, b);
+#else
+    return make_float2(a.x * b.x, a.y * b.y);
+#endif
+}
+__host__ __device__ __forceinline__ float2 operator*(float a, float2 b) { return make_float2(a, a) * b; }
+__host__ __device__ __forceinline__ float2 operator*(float2 a, float b) { return a * make_float2(b, b); }
+__host__ __device__ __forceinline__ float2 &operator+=(float2 &a, float2 b) { return a = a + b; }
+__host__ __device__ __forceinline__ float2 &operator-=(float2 &a, float2 b) { return a = a - b; }
+
+__host__ __device__ __forceinline__ float vfma(float a, float b, float c) { return fmaf(a, b, c); }
+__host__ __device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) {
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+    return __ffma2_rn(a, b, c);
+#else
+    return make_float2(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y));
+#endif
+}
+__host__ __device__ __forceinline__ float vsplat(float a, float) { return a; }
+__host__ __device__ __forceinline__ float2 vsplat(float a, float2) { return make_float2(a, a); }
+// correctly rounded reciprocal
+__host__ __device__ __forceinline__ float vrcp(float a) {
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+    return __frcp_rn(a);
+#else
+    return 1.0f / a;
+#endif
+}
+__host__ __device__ __forceinline__ float2 vrcp(float2 a) { return make_float2(vrcp(a.x), vrcp(a.y)); }
+
+// ------------------------------------------------------------- collision ----
+//
+// Opposite velocity pairs (i, ibar) in paper order: (1,2) (3,4) (5,6) (7,10)
+// (8,9) (11,14) (12,13) (15,18) (16,17) for D3Q19 and (1,2) (3,4) (5,6) for
+// D3Q7.  Every row of M and N is a polynomial that is even or odd in e, so an
+// even moment sees a pair only through s = f_i + f_ibar and an odd moment only
+// through d = f_i - f_ibar; likewise M^T splits into an even part E and an odd
+// part O with f_i+ = f_i - E - O and f_ibar+ = f_ibar - E + O.  The sums below
+// are the rows of M and N of Secs. 2.2-2.3 written over s and d.
+
 // Moments of one node: rho - rho0, rho, u = (sum e f + F/2)/rho, T, and the
 // force F = body force + rho g beta T z-hat (Sec. 2.2).
-struct Macro {
-    float drho, rho, u, v, w, T, Fx, Fy, Fz;
+template <typename V> struct MacroT {
+    V drho, rho, u, v, w, T, Fx, Fy, Fz;
 };
+using Macro = MacroT<float>;
 
-__host__ __device__ __forceinline__ Macro macro_from(const Phys &P, float drho, float jx, float jy, float jz,
-                                                     float T) {
-    Macro m;
-    const float rho = 1.0f + drho;
+template <typename V>
+__host__ __device__ __forceinline__ MacroT<V> macro_from(const Phys &P, V drho, V jx, V jy, V jz, V T) {
+    MacroT<V> m;
+    const V one = vsplat(1.0f, drho);
+    const V rho = one + drho;
     m.drho = drho;
     m.rho = rho;
     m.T = T;
-    m.Fx = P.bf[0];
-    m.Fy = P.bf[1];
-    m.Fz = fmaf(rho * P.gbeta, T, P.bf[2]);
-    const float inv = 1.0f / rho;
-    m.u = fmaf(0.5f, m.Fx, jx) * inv;
-    m.v = fmaf(0.5f, m.Fy, jy) * inv;
-    m.w = fmaf(0.5f, m.Fz, jz) * inv;
+    m.Fx = vsplat(P.bf[0], drho);
+    m.Fy = vsplat(P.bf[1], drho);
+    m.Fz = vfma(P.gbeta * rho, T, vsplat(P.bf[2], drho));
+    const V inv = vrcp(rho);
+    m.u = vfma(vsplat(0.5f, drho), m.Fx, jx) * inv;
+    m.v = vfma(vsplat(0.5f, drho), m.Fy, jy) * inv;
+    m.w = vfma(vsplat(0.5f, drho), m.Fz, jz) * inv;
     return m;
 }
 
-__host__ __device__ __forceinline__ Macro macro(const Phys &P, const float (&f)[19], const float (&g)[7]) {
-    const float dr = f[0] + ((f[1] + f[2]) + (f[3] + f[4]) + (f[5] + f[6])) +
-                     (((f[7] + f[10]) + (f[8] + f[9])) + ((f[11] + f[14]) + (f[12] + f[13])) +
-                      ((f[15] + f[18]) + (f[16] + f[17])));
-    const float jx = (f[1] - f[2]) + ((f[7] - f[10]) - (f[8] - f[9])) + ((f[11] - f[14]) - (f[12] - f[13]));
-    const float jy = (f[3] - f[4]) + ((f[7] - f[10]) + (f[8] - f[9])) + ((f[15] - f[18]) - (f[16] - f[17]));
-    const float jz = (f[5] - f[6]) + ((f[11] - f[14]) + (f[12] - f[13])) + ((f[15] - f[18]) + (f[16] - f[17]));
-    const float T = g[0] + (g[1] + g[2]) + (g[3] + g[4]) + (g[5] + g[6]);
+template <typename V>
+__host__ __device__ __forceinline__ MacroT<V> macro(const Phys &P, const V (&f)[19], const V (&g)[7]) {
+    const V dr = f[0] + ((f[1] + f[2]) + (f[3] + f[4]) + (f[5] + f[6])) +
+                 (((f[7] + f[10]) + (f[8] + f[9])) + ((f[11] + f[14]) + (f[12] + f[13])) +
+                  ((f[15] + f[18]) + (f[16] + f[17])));
+    const V jx = (f[1] - f[2]) + ((f[7] - f[10]) - (f[8] - f[9])) + ((f[11] - f[14]) - (f[12] - f[13]));
+    const V jy = (f[3] - f[4]) + ((f[7] - f[10]) + (f[8] - f[9])) + ((f[15] - f[18]) - (f[16] - f[17]));
+    const V jz = (f[5] - f[6]) + ((f[11] - f[14]) + (f[12] - f[13])) + ((f[15] - f[18]) + (f[16] - f[17]));
+    const V T = g[0] + (g[1] + g[2]) + (g[3] + g[4]) + (g[5] + g[6]);
     return macro_from(P, dr, jx, jy, jz, T);
 }
 
-// One fused collision of both distributions at one node, in place:
+// One fused collision of both distributions at one node (or two nodes for
+// V = float2), in place:
 //   f+ = f - M^-1 [S (m - m^eq) - (I - S/2) M F~]      (Eq. MRT)
 //   g+ = g - N^-1 Q (n - n^eq)                          (Eq. MRT_T)
 // f holds deviations f - w rho0; the rest-state moments M w rho0 =
 // (rho0, -11 rho0, 3 rho0, 0, ...) are folded into m - m^eq below.
 // M^-1 = M^T diag(1/|M_k|^2), N^-1 = N^T diag(1/|N_k|^2).
-__host__ __device__ __forceinline__ Macro collide(const Phys &P, float (&f)[19], float (&g)[7]) {
+template <typename V>
+__host__ __device__ __forceinline__ MacroT<V> collide(const Phys &P, V (&f)[19], V (&g)[7]) {
     constexpr int I[9] = {1, 3, 5, 7, 8, 11, 12, 15, 16};
     constexpr int J[9] = {2, 4, 6, 10, 9, 14, 13, 18, 17};
-    float s[9], d[9];
+    V s[9], d[9];
 #pragma unroll
     for (int p = 0; p < 9; ++p) {
         s[p] = f[I[p]] + f[J[p]];
         d[p] = f[I[p]] - f[J[p]];
     }
-    const float f0 = f[0];
-    const float s34 = s[3] + s[4], s56 = s[5] + s[6], s78 = s[7] + s[8];
-    const float Sax = (s[0] + s[1]) + s[2];
-    const float Sdg = (s34 + s56) + s78;
-    const float dx = (d[3] - d[4]) + (d[5] - d[6]); // diagonal parts of j
-    const float dy = (d[3] + d[4]) + (d[7] - d[8]);
-    const float dz = (d[5] + d[6]) + (d[7] + d[8]);
-    const float gs0 = g[1] + g[2], gs1 = g[3] + g[4], gs2 = g[5] + g[6];
-    const float T = g[0] + (gs0 + gs1) + gs2;
-    const Macro mc = macro_from(P, f0 + Sax + Sdg, d[0] + dx, d[1] + dy, d[2] + dz, T);
-    const float rho = mc.rho, u = mc.u, v = mc.v, w = mc.w;
-    const float Fx = mc.Fx, Fy = mc.Fy, Fz = mc.Fz;
+    const V f0 = f[0];
+    const V s34 = s[3] + s[4], s56 = s[5] + s[6], s78 = s[7] + s[8];
+    const V Sax = (s[0] + s[1]) + s[2];
+    const V Sdg = (s34 + s56) + s78;
+    const V dx = (d[3] - d[4]) + (d[5] - d[6]); // diagonal parts of j
+    const V dy = (d[3] + d[4]) + (d[7] - d[8]);
+    const V dz = (d[5] + d[6]) + (d[7] + d[8]);
+    const V gs0 = g[1] + g[2], gs1 = g[3] + g[4], gs2 = g[5] + g[6];
+    const V T = g[0] + (gs0 + gs1) + gs2;
+    const MacroT<V> mc = macro_from(P, f0 + Sax + Sdg, d[0] + dx, d[1] + dy, d[2] + dz, T);
+    const V rho = mc.rho, u = mc.u, v = mc.v, w = mc.w;
+    const V Fx = mc.Fx, Fy = mc.Fy, Fz = mc.Fz;
 
     // m - m^eq (Sec. 2.2 m^eq) of the non-conserved moments
-    const float uu = u * u + v * v + w * w;
-    const float ru = rho * u, rv = rho * v, rw = rho * w;
-    const float pxx = rho * (2.f * u * u - v * v - w * w);
-    const float pww = rho * (v * v - w * w);
-    const float s3456 = s34 + s56;
-    const float d1 = (-30.f * f0 - 11.f * Sax + 8.f * Sdg) + 11.f * mc.drho - 19.f * rho * uu;
-    const float d2 = (12.f * f0 - 4.f * Sax + Sdg) - 3.f * mc.drho + 5.5f * rho * uu;
-    const float d4 = (-4.f * d[0] + dx) + (2.f / 3.f) * ru;
-    const float d6 = (-4.f * d[1] + dy) + (2.f / 3.f) * rv;
-    const float d8 = (-4.f * d[2] + dz) + (2.f / 3.f) * rw;
-    const float d9 = (2.f * s[0] - s[1] - s[2] + s3456 - 2.f * s78) - pxx;
-    const float d10 = (-4.f * s[0] + 2.f * s[1] + 2.f * s[2] + s3456 - 2.f * s78) + 0.5f * pxx;
-    const float d11 = (s[1] - s[2] + s34 - s56) - pww;
-    const float d12 = (-2.f * s[1] + 2.f * s[2] + s34 - s56) + 0.5f * pww;
-    const float d13 = (s[3] - s[4]) - ru * v;
-    const float d14 = (s[7] - s[8]) - rv * w;
-    const float d15 = (s[5] - s[6]) - ru * w;
-    const float d16 = (d[3] - d[4]) - (d[5] - d[6]);
-    const float d17 = (d[7] - d[8]) - (d[3] + d[4]);
-    const float d18 = (d[5] + d[6]) - (d[7] + d[8]);
+    const V uu = u * u + v * v + w * w;
+    const V ru = rho * u, rv = rho * v, rw = rho * w;
+    const V pxx = rho * (2.f * (u * u) - v * v - w * w);
+    const V pww = rho * (v * v - w * w);
+    const V s3456 = s34 + s56;
+    const V ruu = rho * uu;
+    const V d1 = (-30.f * f0 - 11.f * Sax + 8.f * Sdg) + 11.f * mc.drho - 19.f * ruu;
+    const V d2 = (12.f * f0 - 4.f * Sax + Sdg) - 3.f * mc.drho + 5.5f * ruu;
+    const V d4 = (-4.f * d[0] + dx) + (2.f / 3.f) * ru;
+    const V d6 = (-4.f * d[1] + dy) + (2.f / 3.f) * rv;
+    const V d8 = (-4.f * d[2] + dz) + (2.f / 3.f) * rw;
+    const V d9 = (2.f * s[0] - s[1] - s[2] + s3456 - 2.f * s78) - pxx;
+    const V d10 = (-4.f * s[0] + 2.f * s[1] + 2.f * s[2] + s3456 - 2.f * s78) + 0.5f * pxx;
+    const V d11 = (s[1] - s[2] + s34 - s56) - pww;
+    const V d12 = (-2.f * s[1] + 2.f * s[2] + s34 - s56) + 0.5f * pww;
+    const V d13 = (s[3] - s[4]) - ru * v;
+    const V d14 = (s[7] - s[8]) - rv * w;
+    const V d15 = (s[5] - s[6]) - ru * w;
+    const V d16 = (d[3] - d[4]) - (d[5] - d[6]);
+    const V d17 = (d[7] - d[8]) - (d[3] + d[4]);
+    const V d18 = (d[5] + d[6]) - (d[7] + d[8]);
 
     // a_k, b_k = [S (m - m^eq) - (I - S/2) M F~]_k / |M_k|^2 (even k: a, odd k: b)
-    const float uF = u * Fx + v * Fy + w * Fz;
+    const V uFx = u * Fx, vFy = v * Fy, wFz = w * Fz;
+    const V uF = uFx + vFy + wFz;
     const float se = P.s_e, sq = P.s_q;
     const float ce = 1.f - 0.5f * se, cq = 1.f - 0.5f * sq;
-    const float a1 = (se * d1 - ce * 38.f * uF) * (1.f / 2394.f);
-    const float a2 = (se * d2 + ce * 11.f * uF) * (1.f / 252.f);
-    const float a9 = (se * d9 - ce * (4.f * u * Fx - 2.f * v * Fy - 2.f * w * Fz)) * (1.f / 36.f);
-    const float a10 = (se * d10 - ce * (-2.f * u * Fx + v * Fy + w * Fz)) * (1.f / 72.f);
-    const float a11 = (se * d11 - ce * (2.f * v * Fy - 2.f * w * Fz)) * (1.f / 12.f);
-    const float a12 = (se * d12 - ce * (-v * Fy + w * Fz)) * (1.f / 24.f);
-    const float a13 = (se * d13 - ce * (u * Fy + v * Fx)) * 0.25f;
-    const float a14 = (se * d14 - ce * (v * Fz + w * Fy)) * 0.25f;
-    const float a15 = (se * d15 - ce * (u * Fz + w * Fx)) * 0.25f;
-    const float b3 = -Fx * 0.1f, b5 = -Fy * 0.1f, b7 = -Fz * 0.1f;
-    const float b4 = (sq * d4 + cq * (2.f / 3.f) * Fx) * (1.f / 40.f);
-    const float b6 = (sq * d6 + cq * (2.f / 3.f) * Fy) * (1.f / 40.f);
-    const float b8 = (sq * d8 + cq * (2.f / 3.f) * Fz) * (1.f / 40.f);
-    const float b16 = sq * d16 * 0.125f, b17 = sq * d17 * 0.125f, b18 = sq * d18 * 0.125f;
+    const V a1 = (se * d1 - (ce * 38.f) * uF) * (1.f / 2394.f);
+    const V a2 = (se * d2 + (ce * 11.f) * uF) * (1.f / 252.f);
+    const V a9 = (se * d9 - ce * (4.f * uFx - 2.f * vFy - 2.f * wFz)) * (1.f / 36.f);
+    const V a10 = (se * d10 - ce * (-2.f * uFx + vFy + wFz)) * (1.f / 72.f);
+    const V a11 = (se * d11 - ce * (2.f * vFy - 2.f * wFz)) * (1.f / 12.f);
+    const V a12 = (se * d12 - ce * (wFz - vFy)) * (1.f / 24.f);
+    const V a13 = (se * d13 - ce * (u * Fy + v * Fx)) * 0.25f;
+    const V a14 = (se * d14 - ce * (v * Fz + w * Fy)) * 0.25f;
+    const V a15 = (se * d15 - ce * (u * Fz + w * Fx)) * 0.25f;
+    const V b3 = -0.1f * Fx, b5 = -0.1f * Fy, b7 = -0.1f * Fz;
+    const V b4 = (sq * d4 + (cq * (2.f / 3.f)) * Fx) * (1.f / 40.f);
+    const V b6 = (sq * d6 + (cq * (2.f / 3.f)) * Fy) * (1.f / 40.f);
+    const V b8 = (sq * d8 + (cq * (2.f / 3.f)) * Fz) * (1.f / 40.f);
+    const V b16 = (sq * 0.125f) * d16, b17 = (sq * 0.125f) * d17, b18 = (sq * 0.125f) * d18;
 
     // M^T applied to (a, b): even parts E_p and odd parts O_p of each pair
-    const float Cax = -11.f * a1 - 4.f * a2, Cdg = 8.f * a1 + a2;
-    const float X = a9 + a10, Y = a11 + a12, Z = a11 - 2.f * a12;
-    const float Jx = b3 + b4, Jy = b5 + b6, Jz = b7 + b8;
-    float E[9], O[9];
+    const V Cax = -11.f * a1 - 4.f * a2, Cdg = 8.f * a1 + a2;
+    const V X = a9 + a10, Y = a11 + a12, Z = a11 - 2.f * a12;
+    const V Jx = b3 + b4, Jy = b5 + b6, Jz = b7 + b8;
+    const V CaxX = Cax - a9 + 2.f * a10, CdgXY = Cdg + X + Y, CdgXmY = Cdg + X - Y, Cdg2X = Cdg - 2.f * X;
+    V E[9], O[9];
     E[0] = Cax + 2.f * a9 - 4.f * a10;
-    E[1] = Cax - a9 + 2.f * a10 + Z;
-    E[2] = Cax - a9 + 2.f * a10 - Z;
-    E[3] = Cdg + X + Y + a13;
-    E[4] = Cdg + X + Y - a13;
-    E[5] = Cdg + X - Y + a15;
-    E[6] = Cdg + X - Y - a15;
-    E[7] = Cdg - 2.f * X + a14;
-    E[8] = Cdg - 2.f * X - a14;
+    E[1] = CaxX + Z;
+    E[2] = CaxX - Z;
+    E[3] = CdgXY + a13;
+    E[4] = CdgXY - a13;
+    E[5] = CdgXmY + a15;
+    E[6] = CdgXmY - a15;
+    E[7] = Cdg2X + a14;
+    E[8] = Cdg2X - a14;
     O[0] = b3 - 4.f * b4;
     O[1] = b5 - 4.f * b6;
     O[2] = b7 - 4.f * b8;
     O[3] = Jx + Jy + (b16 - b17);
-    O[4] = -Jx + Jy - (b16 + b17);
+    O[4] = Jy - Jx - (b16 + b17);
     O[5] = Jx + Jz + (b18 - b16);
-    O[6] = -Jx + Jz + (b16 + b18);
+    O[6] = Jz - Jx + (b16 + b18);
     O[7] = Jy + Jz + (b17 - b18);
-    O[8] = -Jy + Jz - (b17 + b18);
+    O[8] = Jz - Jy - (b17 + b18);
+    // f_i = (s + d)/2 and f_ibar = (s - d)/2: the pair sums replace f here, so
+    // the 19 inputs need not stay live through the collision
     f[0] = f0 - (-30.f * a1 + 12.f * a2);
 #pragma unroll
     for (int p = 0; p < 9; ++p) {
-        f[I[p]] -= E[p] + O[p];
-        f[J[p]] -= E[p] - O[p];
+        f[I[p]] = vfma(vsplat(0.5f, f0), s[p] + d[p], -(E[p] + O[p]));
+        f[J[p]] = vfma(vsplat(0.5f, f0), s[p] - d[p], O[p] - E[p]);
     }
 
     // D3Q7: n - n^eq with n^eq = (T, uT, vT, wT, a_T T, 0, 0); |N_k|^2 = 7, 2, 2, 2, 42, 12, 4
-    const float e1 = P.q_k * ((g[1] - g[2]) - u * T) * 0.5f;
-    const float e2 = P.q_k * ((g[3] - g[4]) - v * T) * 0.5f;
-    const float e3 = P.q_k * ((g[5] - g[6]) - w * T) * 0.5f;
-    const float e4 = P.q_e * ((-6.f * g[0] + (gs0 + gs1) + gs2) - P.a_T * T) * (1.f / 42.f);
-    const float e5 = P.q_e * (2.f * gs0 - gs1 - gs2) * (1.f / 12.f);
-    const float e6 = P.q_e * (gs1 - gs2) * 0.25f;
+    const float hk = 0.5f * P.q_k;
+    const V e1 = hk * ((g[1] - g[2]) - u * T);
+    const V e2 = hk * ((g[3] - g[4]) - v * T);
+    const V e3 = hk * ((g[5] - g[6]) - w * T);
+    const V e4 = (P.q_e * (1.f / 42.f)) * ((-6.f * g[0] + (gs0 + gs1) + gs2) - P.a_T * T);
+    const V e5 = (P.q_e * (1.f / 12.f)) * (2.f * gs0 - gs1 - gs2);
+    const V e6 = (P.q_e * 0.25f) * (gs1 - gs2);
     g[0] += 6.f * e4;
-    const float E1 = e4 + 2.f * e5, E2 = e4 - e5 + e6, E3 = e4 - e5 - e6;
+    const V E1 = e4 + 2.f * e5, E2 = e4 - e5 + e6, E3 = e4 - e5 - e6;
     g[1] -= E1 + e1;
     g[2] -= E1 - e1;
     g[3] -= E2 + e2;

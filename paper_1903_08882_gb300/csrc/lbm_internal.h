@@ -18,6 +18,7 @@ struct StepArgs {
     int scheme;   // 0: AA pattern, 1: two-buffer pull
     int parity;   // AA: 0 even step (natural -> reversed), 1 odd step
     int block;    // threads per block
+    int wide;     // AA: 1 = two nodes per thread (packed FP32), 0 = one node per thread
     void *f, *g;  // AA buffer, or pull source
     void *f2, *g2; // pull destination
     Geom G;

@@ -38,6 +38,7 @@ class LbmParams(ctypes.Structure):
         ("body_force", c_double * 3),
         ("wall", LbmWall * 6),
         ("storage", c_int), ("streaming", c_int), ("diag_every", c_int), ("block_size", c_int),
+        ("nodes_per_thread", c_int),
     ]
 
 
@@ -174,7 +175,7 @@ def walls_rayleigh_benard(T_bottom=0.5, T_top=-0.5):
 
 def make_params(nx, ny, nz, walls, Ra=1e6, Pr=0.71, U=0.1, H=0.0, nu=None, kappa=None, gbeta=None,
                 body_force=(0.0, 0.0, 0.0), storage="fp32", streaming="aa", diag_every=0,
-                block_size=0) -> LbmParams:
+                block_size=0, nodes_per_thread=0) -> LbmParams:
     p = LbmParams()
     p.nx, p.ny, p.nz = int(nx), int(ny), int(nz)
     p.Ra, p.Pr, p.U, p.H = float(Ra), float(Pr), float(U), float(H)
@@ -192,6 +193,7 @@ def make_params(nx, ny, nz, walls, Ra=1e6, Pr=0.71, U=0.1, H=0.0, nu=None, kappa
     p.streaming = STREAMING[streaming] if isinstance(streaming, str) else int(streaming)
     p.diag_every = int(diag_every)
     p.block_size = int(block_size)
+    p.nodes_per_thread = int(nodes_per_thread)
     return p
 
 

@@ -84,13 +84,16 @@ WALLS = {
 }
 
 
-@pytest.mark.parametrize("streaming", ["aa", "pull2"])
+@pytest.mark.parametrize("scheme", ["aa1", "aa2", "pull2"])
 @pytest.mark.parametrize("walls", list(WALLS))
-@pytest.mark.parametrize("n", [(5, 6, 7), (13, 11, 12), (3, 3, 3)])
-def test_random_state_steps(lbm, walls, streaming, n):
+@pytest.mark.parametrize("n", [(5, 6, 7), (13, 11, 12), (3, 3, 3), (34, 9, 5)])
+def test_random_state_steps(lbm, walls, scheme, n):
+    """AA with one and two nodes per thread, and the pull scheme."""
     p = _orc_params(n, WALLS[walls])
     f0, g0 = _random_state(p, 3)
-    with _lattice(lbm, n, WALLS[walls], streaming=streaming) as lat:
+    streaming = "pull2" if scheme == "pull2" else "aa"
+    npt = 1 if scheme == "aa1" else 2
+    with _lattice(lbm, n, WALLS[walls], streaming=streaming, nodes_per_thread=npt) as lat:
         lat.set_populations(f0, g0)
         f, g = lat.populations()
         ef, eg = _rel_pop(f, g, f0, g0)
@@ -147,18 +150,22 @@ def test_cfg1_trajectory_2000_steps(lbm):
     assert od["Nu_face"][0] > 1.5  # convection has set in
 
 
+@pytest.mark.parametrize("npt", [1, 2])
 @pytest.mark.parametrize("storage,tol", [("fp16s", 2e-3), ("bf16s", 1.6e-2)])
-def test_reduced_storage_one_step(lbm, storage, tol):
+def test_reduced_storage_one_step(lbm, storage, tol, npt):
     n = (33, 33, 33)
     p = oracle.cell(33, 1e4, 0.71, oracle.side_heated_walls())
     f0, g0 = oracle.init_equilibrium(p, 1.0, np.zeros(3), 0.0)
     f0, g0 = oracle.run(p, f0, g0, 500)
     fo, go = oracle.run(p, f0, g0, 1)
-    with lbm.Lattice(*n, lbm.walls_side_heated(), Ra=1e4, Pr=0.71, storage=storage) as lat:
+    with lbm.Lattice(*n, lbm.walls_side_heated(), Ra=1e4, Pr=0.71, storage=storage,
+                     nodes_per_thread=npt) as lat:
         lat.set_populations(f0, g0)
         lat.step(1)
         e = _rel_fields(lat.moments(), oracle.moments(p, fo, go))
-    assert (e < tol).all(), e
+        lat.step(1)
+        e2 = _rel_fields(lat.moments(), oracle.moments(p, *oracle.run(p, fo, go, 1)))
+    assert (e < tol).all() and (e2 < 2 * tol).all(), (e, e2)
 
 
 def test_diagnostics_parity(lbm):
