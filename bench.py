@@ -298,11 +298,17 @@ def run_gpu(args):
     stream = torch.cuda.Stream()
     peak, peak_kind = _peak_hbm()
     storages = ["fp32"] if args.fp32_only else ["fp32", "fp16s", "bf16s"]
+    if args.only:
+        storages = [args.only]
     results = {}
     with torch.cuda.stream(stream):
         for st in storages:
             results[st] = bench_storage(lbm, st, args, stream, dist, with_e2e=(st == "fp32"))
     if rank != 0:
+        return
+    if "fp32" not in results:  # profiling run of one storage form
+        for st, r in results.items():
+            print(json.dumps({"storage": st, "glups": r["glups"], "kernel_ms": r["kernel_seconds"] * 1e3}))
         return
     main = results["fp32"]
     nodes = N_EDGE ** 3
@@ -354,6 +360,8 @@ def main():
     ap.add_argument("--fp32-only", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--edge", type=int, default=N_EDGE, help="cube edge; other than 257 only for profiling")
+    ap.add_argument("--only", default=None, choices=["fp32", "fp16s", "bf16s"],
+                    help="time one storage form only (profiling)")
     ap.add_argument("--npt", type=int, default=0, help="nodes per thread of the AA kernels (0: library default)")
     args = ap.parse_args()
     N_EDGE = args.edge

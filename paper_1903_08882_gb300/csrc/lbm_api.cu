@@ -326,6 +326,8 @@ lbm_status lbm_create(const lbm_params *params, const lbm_allocator *alloc, void
     G.ni = G.nixy * (uint32_t)(params->nz - 2);
     G.mag_nix = magic_of(G.nix);
     G.mag_nixy = magic_of(G.nixy);
+    G.cpp = ((uint32_t)params->nx * (uint32_t)(params->ny - 2) + 63u) / 64u;
+    G.mag_cpp = magic_of(G.cpp);
     {
         const int ex[19] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
         const int ey[19] = {0, 0, 0, 1, -1, 0, 0, 1, 1, -1, -1, 0, 0, 0, 0, 1, -1, 1, -1};

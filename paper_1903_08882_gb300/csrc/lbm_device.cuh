@@ -113,6 +113,9 @@ struct Geom {
     uint32_t ni, nix, nixy;
     uint64_t mag_nix, mag_nixy;
     int off[19]; // flat offset of e_i: ex + nx ey + nx ny ez
+    // 64-node chunks per z-plane over the rows 1 <= y <= ny-2, and its magic
+    uint32_t cpp;
+    uint64_t mag_cpp;
 };
 
 // Physical constants of one cell (FP32).

@@ -1,7 +1,8 @@
 // Diagnostic reductions: the global quantities of Secs. 3 and 4 from one
 // sample of node moments.
 //
-// Per node (FP32 from the FP32 moment arrays), summed in FP64:
+// Per node (FP32 from the FP32 moment arrays), summed per thread in FP32 with
+// Kahan compensation, then across threads and blocks in FP64:
 //   [0] 1                       [1] (rho - rho0)^2        [2] |u|^2
 //   [3] w^2                     [4] w T                   [5] 1/2 sum_ij (d_i u_j + d_j u_i)^2
 //   [6] |grad T|^2              [7] (div u)^2             [8+f] -dT/dn at Dirichlet face f
@@ -70,12 +71,26 @@ struct WallT {
     float Tw[6];
 };
 
+// Compensated (Kahan) FP32 running sum: FP64 arithmetic is slow on this
+// GPU, and a thread sums only a few dozen nodes, so FP32 with compensation is
+// as accurate as the FP64 block and grid reductions that follow.
+struct KSum {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        const float y = x - c;
+        const float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
 __global__ void __launch_bounds__(kDiagThreads) k_diag(const float *__restrict__ mom, Geom G, Phys P,
                                                        WallT W, double *__restrict__ partial) {
     __shared__ double sh[kDiagThreads / 32][kNDiag];
-    double v[kNDiag];
-#pragma unroll
-    for (int k = 0; k < kNDiag; ++k) v[k] = 0.0;
+    KSum acc[kNDiag];
+    float vmax = 0.f;
+    uint32_t count = 0, bad = 0;
     const int64_t s = G.stride;
     const float *dr = mom, *U = mom + s, *V = mom + 2 * s, *Wv = mom + 3 * s, *T = mom + 4 * s;
     const float *phi[3] = {U, V, Wv};
@@ -104,18 +119,18 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag(const float *__restrict__
                 eps += 0.5f * sij * sij;
             }
         const float dv = du[0][0] + du[1][1] + du[2][2];
-        v[0] += 1.0;
-        v[1] += (double)d * d;
-        v[2] += uu;
-        v[3] += (double)w * w;
-        v[4] += (double)w * t;
-        v[5] += eps;
-        v[6] += gT[0] * gT[0] + gT[1] * gT[1] + gT[2] * gT[2];
-        v[7] += dv * dv;
-        v[14] += t;
-        v[15] += 1.0 + (double)d;
-        v[16] = fmax(v[16], (double)sqrtf(uu));
-        if (!isfinite(uu) || !isfinite(t) || !isfinite(d)) v[17] += 1.0;
+        count += 1;
+        acc[1].add(d * d);
+        acc[2].add(uu);
+        acc[3].add(w * w);
+        acc[4].add(w * t);
+        acc[5].add(eps);
+        acc[6].add(gT[0] * gT[0] + gT[1] * gT[1] + gT[2] * gT[2]);
+        acc[7].add(dv * dv);
+        acc[14].add(t);
+        acc[15].add(d); // sum rho = nodes + sum (rho - rho0)
+        vmax = fmaxf(vmax, sqrtf(uu));
+        if (!isfinite(uu) || !isfinite(t) || !isfinite(d)) bad += 1;
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
 #pragma unroll
@@ -125,12 +140,19 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag(const float *__restrict__
                 if (!at || !((P.dir_mask >> fc) & 1)) continue;
                 const float t1 = T[(int64_t)n + (side == 0 ? b.op[a] : b.om[a])];
                 const float dTdn = (-8.f * W.Tw[fc] + 9.f * t - t1) * (1.f / 3.f);
-                v[8 + fc] += -dTdn;
+                acc[8 + fc].add(-dTdn);
                 const float gin = mom[(5 + fc) * s + n];
-                v[18 + fc] += 2.f * gin - P.abbT[fc];
+                acc[18 + fc].add(2.f * gin - P.abbT[fc]);
             }
         }
     }
+    double v[kNDiag];
+#pragma unroll
+    for (int k = 0; k < kNDiag; ++k) v[k] = acc[k].value();
+    v[0] = (double)count;
+    v[15] += (double)count;
+    v[16] = (double)vmax;
+    v[17] = (double)bad;
     block_reduce(v, sh);
     if (threadIdx.x == 0) {
 #pragma unroll

@@ -225,10 +225,7 @@ __global__ void __launch_bounds__(256, 3) k_aa_odd_face(SE<S> *__restrict__ f, S
 // float2 values with the packed FP32 instructions, halving its instruction
 // count per node.  Even step: nodes 2t and 2t+1 share aligned vector loads
 // and stores (for an odd node count the last pair includes the first padding
-// element, which no real node ever reads).  Odd interior step: interior nodes
-// 2t and 2t+1 of the interior enumeration, loaded element by element; for an
-// odd interior count the last thread updates its node twice with identical
-// values.
+// element, which no real node ever reads).
 
 template <int S, bool MOM>
 __global__ void __launch_bounds__(256, 2) k_aa_even2(SE<S> *__restrict__ f, SE<S> *__restrict__ g, Geom G,
@@ -280,57 +277,78 @@ __device__ __forceinline__ uint32_t interior_node(const Geom &G, uint32_t t) {
     return (xi + 1) + static_cast<uint32_t>(G.nx) * ((yi + 1) + static_cast<uint32_t>(G.ny) * (zi + 1));
 }
 
+// Odd step over the rows with 1 <= y <= ny-2 and 1 <= z <= nz-2, which lie
+// contiguously in each z-plane.  A warp takes 64 consecutive nodes of such a
+// run, lane l the nodes l and l + 32, so every access of the warp is
+// contiguous and the second node's addresses are the first's plus 32.  Nodes
+// at x = 0 or x = nx-1 (and lanes past the end of the run) are left to the
+// face kernel: their loads stay in bounds and their results are not stored.
 template <int S, bool MOM>
-__global__ void __launch_bounds__(256, 2) k_aa_odd_interior2(SE<S> *__restrict__ f, SE<S> *__restrict__ g,
-                                                             Geom G, Phys P, float *__restrict__ mom) {
-    const uint32_t t = 2u * (blockIdx.x * blockDim.x + threadIdx.x);
-    if (t >= G.ni) return;
-    const uint32_t n0 = interior_node(G, t);
-    const uint32_t n1 = interior_node(G, t + 1 < G.ni ? t + 1 : t);
+__global__ void __launch_bounds__(256, 2) k_aa_odd_rows(SE<S> *__restrict__ f, SE<S> *__restrict__ g, Geom G,
+                                                        Phys P, float *__restrict__ mom) {
+    const uint32_t warp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const uint32_t lane = threadIdx.x & 31u;
+    const uint32_t zi = fast_div(warp, G.mag_cpp);
+    if (zi >= static_cast<uint32_t>(G.nz - 2)) return;
+    const uint32_t c = warp - zi * G.cpp;
+    const uint32_t nx = static_cast<uint32_t>(G.nx);
+    const uint32_t len = nx * static_cast<uint32_t>(G.ny - 2);
+    const uint32_t o0 = c * 64u + lane;
+    const uint32_t n0 = nx * (1u + static_cast<uint32_t>(G.ny) * (zi + 1u)) + o0;
+    const uint32_t x0 = n0 - nx * fast_div(n0, G.mag_nx);
+    const uint32_t x1 = (n0 + 32u) - nx * fast_div(n0 + 32u, G.mag_nx);
+    const bool a0 = o0 < len && x0 != 0u && x0 != nx - 1u;
+    const bool a1 = o0 + 32u < len && x1 != 0u && x1 != nx - 1u;
+    if (!a0 && !a1) return;
     const int64_t s = G.stride;
     float2 fl[19], gl[7];
-    fl[0] = make_float2(Store<S>::ld(f + n0), Store<S>::ld(f + n1));
+    fl[0] = make_float2(Store<S>::ld(f + n0), Store<S>::ld(f + n0 + 32));
 #pragma unroll
     for (int i = 1; i < 19; ++i) {
-        const SE<S> *q = f + opp19(i) * s;
-        fl[i] = make_float2(Store<S>::ld(q + (int64_t)(n0 - G.off[i])), Store<S>::ld(q + (int64_t)(n1 - G.off[i])));
+        const SE<S> *q = f + opp19(i) * s + (int64_t)(n0 - G.off[i]);
+        fl[i] = make_float2(Store<S>::ld(q), Store<S>::ld(q + 32));
     }
-    gl[0] = make_float2(Store<S>::ld(g + n0), Store<S>::ld(g + n1));
+    gl[0] = make_float2(Store<S>::ld(g + n0), Store<S>::ld(g + n0 + 32));
 #pragma unroll
     for (int i = 1; i < 7; ++i) {
-        const SE<S> *q = g + opp7(i) * s;
-        gl[i] = make_float2(Store<S>::ld(q + (int64_t)(n0 - G.off[i])), Store<S>::ld(q + (int64_t)(n1 - G.off[i])));
+        const SE<S> *q = g + opp7(i) * s + (int64_t)(n0 - G.off[i]);
+        gl[i] = make_float2(Store<S>::ld(q), Store<S>::ld(q + 32));
     }
     const MacroT<float2> m = collide(P, fl, gl);
     f = opaque(f);
     g = opaque(g);
-    Store<S>::st(f + n0, fl[0].x);
-    Store<S>::st(f + n1, fl[0].y);
+    if (a0) Store<S>::st(f + n0, fl[0].x);
+    if (a1) Store<S>::st(f + n0 + 32, fl[0].y);
 #pragma unroll
     for (int i = 1; i < 19; ++i) {
-        SE<S> *q = f + i * s;
-        Store<S>::st(q + (int64_t)(n0 + G.off[i]), fl[i].x);
-        Store<S>::st(q + (int64_t)(n1 + G.off[i]), fl[i].y);
+        SE<S> *q = f + i * s + (int64_t)(n0 + G.off[i]);
+        if (a0) Store<S>::st(q, fl[i].x);
+        if (a1) Store<S>::st(q + 32, fl[i].y);
     }
-    Store<S>::st(g + n0, gl[0].x);
-    Store<S>::st(g + n1, gl[0].y);
+    if (a0) Store<S>::st(g + n0, gl[0].x);
+    if (a1) Store<S>::st(g + n0 + 32, gl[0].y);
 #pragma unroll
     for (int i = 1; i < 7; ++i) {
-        SE<S> *q = g + i * s;
-        Store<S>::st(q + (int64_t)(n0 + G.off[i]), gl[i].x);
-        Store<S>::st(q + (int64_t)(n1 + G.off[i]), gl[i].y);
+        SE<S> *q = g + i * s + (int64_t)(n0 + G.off[i]);
+        if (a0) Store<S>::st(q, gl[i].x);
+        if (a1) Store<S>::st(q + 32, gl[i].y);
     }
     if (MOM) {
-        mom[n0] = m.drho.x;
-        mom[s + n0] = m.u.x;
-        mom[2 * s + n0] = m.v.x;
-        mom[3 * s + n0] = m.w.x;
-        mom[4 * s + n0] = m.T.x;
-        mom[n1] = m.drho.y;
-        mom[s + n1] = m.u.y;
-        mom[2 * s + n1] = m.v.y;
-        mom[3 * s + n1] = m.w.y;
-        mom[4 * s + n1] = m.T.y;
+        if (a0) {
+            mom[n0] = m.drho.x;
+            mom[s + n0] = m.u.x;
+            mom[2 * s + n0] = m.v.x;
+            mom[3 * s + n0] = m.w.x;
+            mom[4 * s + n0] = m.T.x;
+        }
+        if (a1) {
+            const uint32_t n1 = n0 + 32u;
+            mom[n1] = m.drho.y;
+            mom[s + n1] = m.u.y;
+            mom[2 * s + n1] = m.v.y;
+            mom[3 * s + n1] = m.w.y;
+            mom[4 * s + n1] = m.T.y;
+        }
     }
 }
 
@@ -487,12 +505,13 @@ static cudaError_t step_t(const StepArgs &a) {
             if (a.mom) k_aa_even2<S, true><<<nb2, a.block, 0, a.stream>>>(f, g, a.G, a.P, a.mom);
             else k_aa_even2<S, false><<<nb2, a.block, 0, a.stream>>>(f, g, a.G, a.P, nullptr);
         } else {
-            const unsigned ni = blocks_for((a.G.ni + 1) / 2, a.block), nf = blocks_for(a.nface, a.block);
+            const unsigned nwarps = a.G.cpp * (unsigned)(a.G.nz - 2);
+            const unsigned ni = blocks_for(nwarps, a.block / 32), nf = blocks_for(a.nface, a.block);
             if (a.mom) {
-                if (ni) k_aa_odd_interior2<S, true><<<ni, a.block, 0, a.stream>>>(f, g, a.G, a.P, a.mom);
+                if (ni) k_aa_odd_rows<S, true><<<ni, a.block, 0, a.stream>>>(f, g, a.G, a.P, a.mom);
                 if (nf) k_aa_odd_face<S, true><<<nf, a.block, 0, a.stream>>>(f, g, a.G, a.P, a.mom, a.face, a.nface);
             } else {
-                if (ni) k_aa_odd_interior2<S, false><<<ni, a.block, 0, a.stream>>>(f, g, a.G, a.P, nullptr);
+                if (ni) k_aa_odd_rows<S, false><<<ni, a.block, 0, a.stream>>>(f, g, a.G, a.P, nullptr);
                 if (nf)
                     k_aa_odd_face<S, false><<<nf, a.block, 0, a.stream>>>(f, g, a.G, a.P, nullptr, a.face, a.nface);
             }
