@@ -319,7 +319,8 @@ def run_gpu(args):
                 "frac": round(ach / peak, 4), "peak_kind": peak_kind,
                 "frac_of_nominal_8000": round(ach / NOMINAL_HBM_GBS, 4),
                 "algorithmic_bytes_per_launch": BYTES_PER_NODE[st] * nodes,
-                "traffic": _profiled_traffic(st), "kernel": f"step kernel (AA pattern, {st} storage)",
+                "traffic": _profiled_traffic(st),
+                "kernel": f"one AA LB time step, {st} storage (k_aa_even2, or k_aa_odd_rows + k_aa_odd_face)",
                 "kernel_ms": round(r["kernel_seconds"] * 1e3, 4),
                 "kernel_glups": round(nodes / r["kernel_seconds"] / 1e9, 3)}
 
