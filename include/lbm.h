@@ -221,6 +221,53 @@ lbm_status lbm_load(lbm_ctx *ctx, const char *path);
  * lbm_get_populations to read them in a defined layout. */
 lbm_status lbm_device_view(lbm_ctx *ctx, void **f, void **g, int64_t *stride, int *elem_bytes);
 
+/* ------------------------------------------------------------------ batches --
+ * Many independent cells advanced together (no counterpart in the paper, whose
+ * runs are single cells).  A batch borrows existing contexts; each must use
+ * the AA streaming scheme and all must share one storage format.  One batch
+ * step advances every cell by one time step inside one persistent,
+ * cooperative kernel launch: the cells' tiles (a block's share of one cell's
+ * step) are listed per step parity, the blocks stride over the list, and a
+ * grid-wide barrier separates time steps.  Runs of graph_chunk steps are
+ * captured once into a CUDA graph and replayed. */
+typedef struct lbm_batch lbm_batch;
+
+/* Schedule of the persistent launch. */
+typedef struct {
+    int block_size;    /* 128 or 256 threads */
+    int blocks_per_sm; /* resident blocks per SM (capped by occupancy); grid = SMs x this */
+    int steps_per_launch; /* time steps inside one launch (a launch boundary also synchronises) */
+    int graph_chunk;   /* steps per captured graph (a multiple of steps_per_launch, even); 0 = no graph */
+} lbm_schedule;
+
+/* Create a batch over `ncells` contexts (borrowed: they must outlive the
+ * batch and not be stepped on their own while it is in use).  stream: the
+ * cudaStream_t of the batch launches (NULL: legacy default stream).  Errors:
+ * LBM_ERR_PARAM (a context uses pull streaming, storage formats differ, or
+ * ncells < 1); lbm_last_error(NULL) describes it. */
+lbm_status lbm_batch_create(lbm_ctx *const *cells, int ncells, void *stream, lbm_batch **out);
+void lbm_batch_destroy(lbm_batch *batch);
+
+/* Advance every cell by n time steps.  All cells must be at the same step
+ * parity (LBM_ERR_STATE otherwise; lbm_set_fields / lbm_set_populations put a
+ * cell at parity 0).  Diagnostics are not sampled inside a batch step; call
+ * lbm_sample on a cell afterwards.  Synchronises the stream and returns
+ * LBM_ERR_TIMEOUT if a grid-barrier wait ran out of its cycle budget (the
+ * cells' states are then undefined). */
+lbm_status lbm_batch_step(lbm_batch *batch, int64_t n);
+
+lbm_status lbm_batch_get_schedule(const lbm_batch *batch, lbm_schedule *out);
+lbm_status lbm_batch_set_schedule(lbm_batch *batch, const lbm_schedule *s);
+
+/* Time each candidate schedule (block size 128/256, 1-3 blocks per SM) over
+ * `trial_steps` steps and keep the fastest; the trials advance the cells.
+ * *best receives it when non-NULL. */
+lbm_status lbm_batch_autotune(lbm_batch *batch, int trial_steps, lbm_schedule *best);
+
+/* Cycle budget of one grid-barrier wait (default 2^31 cycles, about a second).
+ * A budget of 0 makes any wait fail at once: used to test the timeout path. */
+lbm_status lbm_batch_set_barrier_budget(lbm_batch *batch, int64_t cycles);
+
 /* Allocation-free diagnostics reduction.  The paper has no counterpart.
  *
  * Some callers cannot allocate device memory at the moment they need the

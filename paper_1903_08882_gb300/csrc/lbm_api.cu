@@ -675,3 +675,327 @@ lbm_status lbm_device_view(lbm_ctx *ctx, void **f, void **g, int64_t *stride, in
 }
 
 } // extern "C"
+
+// ------------------------------------------------------------------ batches --
+
+struct lbm_batch {
+    std::vector<lbm_ctx *> cells;
+    int storage = 0;
+    int dev = 0;
+    int nsm = 0;
+    cudaStream_t stream = nullptr;
+    lbm_schedule sched{256, 1, 100, 1000};
+    long long budget = 1LL << 31;
+    CellDev *d_cells = nullptr;
+    Tile *d_tiles = nullptr; // even tiles, then odd tiles
+    size_t tiles_bytes = 0;
+    GridBarrier *d_bar = nullptr;
+    int n_even = 0, n_odd = 0, tiles_block = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    lbm_schedule graph_sched{};
+    int graph_parity = -1;
+    long long graph_budget = 0;
+    std::string err;
+};
+
+namespace {
+
+lbm_status bfail(lbm_batch *b, lbm_status s, const std::string &msg) {
+    if (b) b->err = msg;
+    g_create_error = msg;
+    return s;
+}
+
+#define BCK(b, call)                                                                            \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess)                                                                  \
+            return bfail(b, LBM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));  \
+    } while (0)
+
+void drop_graph(lbm_batch *b) {
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->gexec = nullptr;
+    b->graph = nullptr;
+    b->graph_parity = -1;
+}
+
+// Tile lists for a block size: per cell, the blocks of its single-cell kernels.
+lbm_status build_tiles(lbm_batch *b, int block) {
+    std::vector<Tile> even, odd;
+    for (int c = 0; c < (int)b->cells.size(); ++c) {
+        const lbm_ctx *x = b->cells[c];
+        const Geom &G = x->G;
+        const uint32_t ne = (uint32_t)(((uint64_t)G.n + 1) / 2 + block - 1) / block;
+        for (uint32_t k = 0; k < ne; ++k) even.push_back({c, TILE_EVEN, k});
+        const uint64_t warps = (uint64_t)G.cpp * (uint64_t)(G.nz - 2);
+        const uint32_t nr = (uint32_t)((warps + block / 32 - 1) / (block / 32));
+        for (uint32_t k = 0; k < nr; ++k) odd.push_back({c, TILE_ROWS, k});
+        const uint32_t nf = (x->nface + block - 1) / block;
+        for (uint32_t k = 0; k < nf; ++k) odd.push_back({c, TILE_FACE, k});
+    }
+    const size_t bytes = (even.size() + odd.size()) * sizeof(Tile);
+    lbm_ctx *a = b->cells[0];
+    if (bytes > b->tiles_bytes) {
+        cudaStreamSynchronize(b->stream);
+        a->dfree(b->d_tiles, b->tiles_bytes);
+        b->d_tiles = (Tile *)a->dalloc(bytes);
+        b->tiles_bytes = b->d_tiles ? bytes : 0;
+        if (!b->d_tiles) return bfail(b, LBM_ERR_OOM, "tile table allocation failed");
+    }
+    BCK(b, cudaMemcpyAsync(b->d_tiles, even.data(), even.size() * sizeof(Tile), cudaMemcpyHostToDevice, b->stream));
+    BCK(b, cudaMemcpyAsync(b->d_tiles + even.size(), odd.data(), odd.size() * sizeof(Tile), cudaMemcpyHostToDevice,
+                           b->stream));
+    BCK(b, cudaStreamSynchronize(b->stream));
+    b->n_even = (int)even.size();
+    b->n_odd = (int)odd.size();
+    b->tiles_block = block;
+    return LBM_OK;
+}
+
+lbm_status grid_for(lbm_batch *b, const lbm_schedule &s, int *grid) {
+    int occ = 0;
+    BCK(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel_ptr(b->storage, s.block_size),
+                                                        s.block_size, 0));
+    if (occ < 1) return bfail(b, LBM_ERR_PARAM, "batched kernel does not fit on an SM with this block size");
+    *grid = b->nsm * (s.blocks_per_sm < occ ? s.blocks_per_sm : occ);
+    return LBM_OK;
+}
+
+BatchArgs batch_args(lbm_batch *b, int grid, int nsteps, int parity0) {
+    BatchArgs a{};
+    a.cells = b->d_cells;
+    a.even = b->d_tiles;
+    a.odd = b->d_tiles + b->n_even;
+    a.n_even = b->n_even;
+    a.n_odd = b->n_odd;
+    a.nsteps = nsteps;
+    a.parity0 = parity0;
+    a.bar = b->d_bar;
+    a.budget = b->budget;
+    a.grid = grid;
+    a.block = b->sched.block_size;
+    a.stream = b->stream;
+    return a;
+}
+
+lbm_status check_schedule(lbm_batch *b, const lbm_schedule &s) {
+    if (s.block_size != 128 && s.block_size != 256) return bfail(b, LBM_ERR_PARAM, "block_size must be 128 or 256");
+    if (s.blocks_per_sm < 1 || s.blocks_per_sm > 8) return bfail(b, LBM_ERR_PARAM, "blocks_per_sm must be in [1, 8]");
+    if (s.steps_per_launch < 1) return bfail(b, LBM_ERR_PARAM, "steps_per_launch must be >= 1");
+    if (s.graph_chunk < 0 || (s.graph_chunk > 0 && (s.graph_chunk % s.steps_per_launch || s.graph_chunk % 2)))
+        return bfail(b, LBM_ERR_PARAM, "graph_chunk must be 0 or an even multiple of steps_per_launch");
+    return LBM_OK;
+}
+
+} // namespace
+
+extern "C" {
+
+lbm_status lbm_batch_create(lbm_ctx *const *cells, int ncells, void *stream, lbm_batch **out) {
+    if (!out) return bfail(nullptr, LBM_ERR_PARAM, "out is NULL");
+    *out = nullptr;
+    if (!cells || ncells < 1) return bfail(nullptr, LBM_ERR_PARAM, "need at least one cell");
+    for (int c = 0; c < ncells; ++c) {
+        if (!cells[c]) return bfail(nullptr, LBM_ERR_PARAM, "NULL cell");
+        if (cells[c]->p.streaming != LBM_STREAM_AA)
+            return bfail(nullptr, LBM_ERR_PARAM, "batched cells must use the AA streaming scheme");
+        if (cells[c]->p.storage != cells[0]->p.storage)
+            return bfail(nullptr, LBM_ERR_PARAM, "batched cells must share one storage format");
+        if (cells[c]->dev != cells[0]->dev) return bfail(nullptr, LBM_ERR_PARAM, "batched cells must share one device");
+    }
+    lbm_batch *b = new lbm_batch();
+    b->cells.assign(cells, cells + ncells);
+    b->storage = cells[0]->p.storage;
+    b->dev = cells[0]->dev;
+    b->stream = static_cast<cudaStream_t>(stream);
+    DeviceGuard dg(b->dev);
+    if (cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, b->dev) != cudaSuccess || b->nsm < 1) {
+        delete b;
+        return bfail(nullptr, LBM_ERR_CUDA, "cannot query the SM count");
+    }
+    int coop = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, b->dev);
+    if (!coop) {
+        delete b;
+        return bfail(nullptr, LBM_ERR_CUDA, "device does not support cooperative launches");
+    }
+    if (!stream) b->sched.graph_chunk = 0; // the legacy default stream cannot be captured
+    std::vector<CellDev> cd(ncells);
+    for (int c = 0; c < ncells; ++c) {
+        lbm_ctx *x = cells[c];
+        cd[c].G = x->G;
+        cd[c].P = x->P;
+        cd[c].f = x->fbase(0);
+        cd[c].g = x->gbase(0);
+        cd[c].face = x->face;
+        cd[c].nface = x->nface;
+    }
+    lbm_ctx *a = cells[0];
+    b->d_cells = (CellDev *)a->dalloc(cd.size() * sizeof(CellDev));
+    b->d_bar = (GridBarrier *)a->dalloc(sizeof(GridBarrier));
+    if (!b->d_cells || !b->d_bar) {
+        a->dfree(b->d_cells, cd.size() * sizeof(CellDev));
+        a->dfree(b->d_bar, sizeof(GridBarrier));
+        delete b;
+        return bfail(nullptr, LBM_ERR_OOM, "batch table allocation failed");
+    }
+    cudaError_t e = cudaMemcpyAsync(b->d_cells, cd.data(), cd.size() * sizeof(CellDev), cudaMemcpyHostToDevice,
+                                    b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_bar, 0, sizeof(GridBarrier), b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    lbm_status st = e == cudaSuccess ? build_tiles(b, b->sched.block_size)
+                                     : bfail(b, LBM_ERR_CUDA, std::string("batch set-up: ") + cudaGetErrorString(e));
+    if (st != LBM_OK) {
+        lbm_batch_destroy(b);
+        g_create_error = "batch set-up failed";
+        return st;
+    }
+    *out = b;
+    return LBM_OK;
+}
+
+void lbm_batch_destroy(lbm_batch *b) {
+    if (!b) return;
+    DeviceGuard dg(b->dev);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    drop_graph(b);
+    lbm_ctx *a = b->cells.empty() ? nullptr : b->cells[0];
+    if (a) {
+        a->dfree(b->d_cells, b->cells.size() * sizeof(CellDev));
+        a->dfree(b->d_tiles, b->tiles_bytes);
+        a->dfree(b->d_bar, sizeof(GridBarrier));
+    }
+    delete b;
+}
+
+lbm_status lbm_batch_get_schedule(const lbm_batch *b, lbm_schedule *out) {
+    if (!b || !out) return LBM_ERR_PARAM;
+    *out = b->sched;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_set_schedule(lbm_batch *b, const lbm_schedule *s) {
+    if (!b || !s) return LBM_ERR_PARAM;
+    lbm_status st = check_schedule(b, *s);
+    if (st != LBM_OK) return st;
+    DeviceGuard dg(b->dev);
+    b->sched = *s;
+    if (!b->stream) b->sched.graph_chunk = 0;
+    drop_graph(b);
+    if (b->tiles_block != s->block_size) return build_tiles(b, s->block_size);
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_set_barrier_budget(lbm_batch *b, int64_t cycles) {
+    if (!b || cycles < 0) return LBM_ERR_PARAM;
+    b->budget = cycles;
+    drop_graph(b);
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_step(lbm_batch *b, int64_t n) {
+    if (!b) return LBM_ERR_PARAM;
+    if (n < 0) return bfail(b, LBM_ERR_PARAM, "negative step count");
+    const int p0 = b->cells[0]->parity;
+    for (lbm_ctx *c : b->cells)
+        if (c->parity != p0) return bfail(b, LBM_ERR_STATE, "batched cells are at different step parities");
+    DeviceGuard dg(b->dev);
+    int grid = 0;
+    lbm_status st = grid_for(b, b->sched, &grid);
+    if (st != LBM_OK) return st;
+    int parity = p0;
+    int64_t left = n;
+    const int chunk = b->sched.graph_chunk, spl = b->sched.steps_per_launch;
+    if (chunk > 0 && left >= chunk) {
+        if (!b->gexec || b->graph_parity != parity || b->graph_budget != b->budget ||
+            std::memcmp(&b->graph_sched, &b->sched, sizeof(lbm_schedule)) != 0) {
+            drop_graph(b);
+            BCK(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = cudaSuccess;
+            for (int k = 0; k < chunk / spl && e == cudaSuccess; ++k)
+                e = launch_batch(b->storage, batch_args(b, grid, spl, parity + k * spl));
+            cudaGraph_t g = nullptr;
+            cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+            if (e != cudaSuccess || e2 != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                return bfail(b, LBM_ERR_CUDA, std::string("graph capture: ") +
+                                                  cudaGetErrorString(e != cudaSuccess ? e : e2));
+            }
+            b->graph = g;
+            BCK(b, cudaGraphInstantiate(&b->gexec, b->graph, 0));
+            b->graph_sched = b->sched;
+            b->graph_parity = parity;
+            b->graph_budget = b->budget;
+        }
+        while (left >= chunk) {
+            BCK(b, cudaGraphLaunch(b->gexec, b->stream));
+            left -= chunk;
+        }
+    }
+    while (left > 0) {
+        const int k = (int)(left < spl ? left : spl);
+        BCK(b, launch_batch(b->storage, batch_args(b, grid, k, parity)));
+        parity ^= k & 1;
+        left -= k;
+    }
+    GridBarrier hb{};
+    BCK(b, cudaMemcpyAsync(&hb, b->d_bar, sizeof(hb), cudaMemcpyDeviceToHost, b->stream));
+    BCK(b, cudaStreamSynchronize(b->stream));
+    for (lbm_ctx *c : b->cells) {
+        c->step += n;
+        c->parity ^= (int)(n & 1);
+    }
+    if (hb.err) {
+        BCK(b, cudaMemsetAsync(b->d_bar, 0, sizeof(GridBarrier), b->stream));
+        BCK(b, cudaStreamSynchronize(b->stream));
+        return bfail(b, LBM_ERR_TIMEOUT, "a grid-barrier wait ran out of its cycle budget; cell states are undefined");
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_autotune(lbm_batch *b, int trial_steps, lbm_schedule *best) {
+    if (!b || trial_steps < 2) return b ? bfail(b, LBM_ERR_PARAM, "trial_steps must be >= 2") : LBM_ERR_PARAM;
+    DeviceGuard dg(b->dev);
+    const lbm_schedule keep = b->sched;
+    lbm_schedule win = keep;
+    float best_ms = 1e30f;
+    cudaEvent_t e0, e1;
+    BCK(b, cudaEventCreate(&e0));
+    BCK(b, cudaEventCreate(&e1));
+    const int blocks[2] = {128, 256};
+    lbm_status st = LBM_OK;
+    for (int bi = 0; bi < 2 && st == LBM_OK; ++bi) {
+        for (int bps = 1; bps <= 3 && st == LBM_OK; ++bps) {
+            lbm_schedule s{blocks[bi], bps, keep.steps_per_launch, 0};
+            int occ = 0;
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel_ptr(b->storage, s.block_size),
+                                                          s.block_size, 0);
+            if (bps > occ) continue;
+            if ((st = lbm_batch_set_schedule(b, &s)) != LBM_OK) break;
+            if ((st = lbm_batch_step(b, 2)) != LBM_OK) break; // warm-up
+            cudaEventRecord(e0, b->stream);
+            if ((st = lbm_batch_step(b, trial_steps)) != LBM_OK) break;
+            cudaEventRecord(e1, b->stream);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best_ms) {
+                best_ms = ms;
+                win = s;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != LBM_OK) return st;
+    win.steps_per_launch = keep.steps_per_launch;
+    win.graph_chunk = keep.graph_chunk;
+    st = lbm_batch_set_schedule(b, &win);
+    if (best) *best = b->sched;
+    return st;
+}
+
+} // extern "C"

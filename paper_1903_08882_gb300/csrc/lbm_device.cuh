@@ -199,6 +199,41 @@ __host__ __device__ constexpr int face_of(int ex, int ey, int ez) {
 // part O with f_i+ = f_i - E - O and f_ibar+ = f_ibar - E + O.  The sums below
 // are the rows of M and N of Secs. 2.2-2.3 written over s and d.
 
+// ----------------------------------------------------- grid-wide barrier ----
+//
+// All blocks of a cooperative launch arrive on a counter; the last one resets
+// it and advances the generation that the others wait on.  Each wait gives up
+// after `budget` clock cycles, raises the shared error flag and lets every
+// block leave; the caller reads the flag after the launch.  Returns false once
+// the flag is up.
+template <typename B> __device__ __forceinline__ bool grid_barrier(B *bar, unsigned nblocks, long long budget) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *gen = &bar->gen;
+        volatile int *err = &bar->err;
+        const unsigned g0 = *gen;
+        __threadfence();
+        if (atomicAdd(&bar->count, 1u) == nblocks - 1u) {
+            atomicExch(&bar->count, 0u);
+            __threadfence();
+            atomicAdd(&bar->gen, 1u);
+        } else {
+            const long long t0 = clock64();
+            while (*gen == g0) {
+                if (*err) break;
+                if (clock64() - t0 > budget) {
+                    atomicExch(&bar->err, 1);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return *reinterpret_cast<volatile int *>(&bar->err) == 0;
+}
+
 // ------------------------------------------------------ vector arithmetic ----
 //
 // The collision is written once for a value type V: float (one node per

@@ -45,6 +45,37 @@ int diag_blocks(const Geom &G);
 cudaError_t launch_diag(const float *mom, const Geom &G, const Phys &P, const float *wallT,
                         double *partial, int nblocks, double *raw, double *acc, cudaStream_t stream);
 
+// ---- batched persistent launch ----
+struct CellDev {
+    Geom G;
+    Phys P;
+    void *f, *g;          // AA population buffer of the cell (f arrays, then g arrays)
+    const uint32_t *face; // nodes next to a face
+    uint32_t nface;
+};
+enum TileKind { TILE_EVEN = 0, TILE_ROWS = 1, TILE_FACE = 2 };
+struct Tile {
+    int cell, kind;
+    uint32_t blk; // block index of the single-cell kernel this tile stands for
+};
+struct GridBarrier {
+    unsigned count, gen;
+    int err; // 1: a wait ran out of its cycle budget
+    int pad;
+};
+struct BatchArgs {
+    const CellDev *cells;
+    const Tile *even, *odd;
+    int n_even, n_odd, nsteps, parity0;
+    GridBarrier *bar;
+    long long budget;
+    int grid, block;
+    cudaStream_t stream;
+};
+// block is 128 or 256 threads (two compiled variants)
+const void *batch_kernel_ptr(int storage, int block);
+cudaError_t launch_batch(int storage, const BatchArgs &a);
+
 // Sets the message lbm_last_error(NULL) returns.
 void set_global_error(const std::string &msg);
 

@@ -165,10 +165,10 @@ __global__ void __launch_bounds__(256, 3) k_aa_odd_interior(SE<S> *__restrict__ 
 
 // Nodes next to a face, listed in `list`.
 template <int S, bool MOM>
-__global__ void __launch_bounds__(256, 3) k_aa_odd_face(SE<S> *__restrict__ f, SE<S> *__restrict__ g, Geom G,
-                                                        Phys P, float *__restrict__ mom,
-                                                        const uint32_t *__restrict__ list, uint32_t count) {
-    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void k_aa_odd_face_tile(SE<S> *__restrict__ f, SE<S> *__restrict__ g, const Geom &G,
+                                                        const Phys &P, float *__restrict__ mom,
+                                                        const uint32_t *__restrict__ list, uint32_t count, uint32_t blk, uint32_t tid, uint32_t bdim) {
+    const uint32_t t = blk * bdim + tid;
     if (t >= count) return;
     const uint32_t n = list[t];
     const int64_t s = G.stride;
@@ -219,6 +219,13 @@ __global__ void __launch_bounds__(256, 3) k_aa_odd_face(SE<S> *__restrict__ f, S
     if (MOM) write_sample(mom, s, n, m, b, g0);
 }
 
+template <int S, bool MOM>
+__global__ void __launch_bounds__(256, 3) k_aa_odd_face(SE<S> *__restrict__ f, SE<S> *__restrict__ g, Geom G,
+                                                        Phys P, float *__restrict__ mom,
+                                                        const uint32_t *__restrict__ list, uint32_t count) {
+    k_aa_odd_face_tile<S, MOM>(f, g, G, P, mom, list, count, blockIdx.x, threadIdx.x, blockDim.x);
+}
+
 // ------------------------------------------- two nodes per thread (f32x2) ----
 //
 // The same updates with one thread per two nodes: the collision runs on
@@ -228,9 +235,9 @@ __global__ void __launch_bounds__(256, 3) k_aa_odd_face(SE<S> *__restrict__ f, S
 // element, which no real node ever reads).
 
 template <int S, bool MOM>
-__global__ void __launch_bounds__(256, 2) k_aa_even2(SE<S> *__restrict__ f, SE<S> *__restrict__ g, Geom G,
-                                                     Phys P, float *__restrict__ mom) {
-    const uint32_t n = 2u * (blockIdx.x * blockDim.x + threadIdx.x);
+__device__ __forceinline__ void k_aa_even2_tile(SE<S> *__restrict__ f, SE<S> *__restrict__ g, const Geom &G,
+                                                     const Phys &P, float *__restrict__ mom, uint32_t blk, uint32_t tid, uint32_t bdim) {
+    const uint32_t n = 2u * (blk * bdim + tid);
     if (n >= G.n) return;
     const int64_t s = G.stride;
     float2 fl[19], gl[7];
@@ -269,6 +276,12 @@ __global__ void __launch_bounds__(256, 2) k_aa_even2(SE<S> *__restrict__ f, SE<S
     }
 }
 
+template <int S, bool MOM>
+__global__ void __launch_bounds__(256, 2) k_aa_even2(SE<S> *__restrict__ f, SE<S> *__restrict__ g, Geom G,
+                                                     Phys P, float *__restrict__ mom) {
+    k_aa_even2_tile<S, MOM>(f, g, G, P, mom, blockIdx.x, threadIdx.x, blockDim.x);
+}
+
 __device__ __forceinline__ uint32_t interior_node(const Geom &G, uint32_t t) {
     const uint32_t zi = fast_div(t, G.mag_nixy);
     const uint32_t r = t - zi * G.nixy;
@@ -284,10 +297,10 @@ __device__ __forceinline__ uint32_t interior_node(const Geom &G, uint32_t t) {
 // at x = 0 or x = nx-1 (and lanes past the end of the run) are left to the
 // face kernel: their loads stay in bounds and their results are not stored.
 template <int S, bool MOM>
-__global__ void __launch_bounds__(256, 2) k_aa_odd_rows(SE<S> *__restrict__ f, SE<S> *__restrict__ g, Geom G,
-                                                        Phys P, float *__restrict__ mom) {
-    const uint32_t warp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const uint32_t lane = threadIdx.x & 31u;
+__device__ __forceinline__ void k_aa_odd_rows_tile(SE<S> *__restrict__ f, SE<S> *__restrict__ g, const Geom &G,
+                                                        const Phys &P, float *__restrict__ mom, uint32_t blk, uint32_t tid, uint32_t bdim) {
+    const uint32_t warp = blk * (bdim >> 5) + (tid >> 5);
+    const uint32_t lane = tid & 31u;
     const uint32_t zi = fast_div(warp, G.mag_cpp);
     if (zi >= static_cast<uint32_t>(G.nz - 2)) return;
     const uint32_t c = warp - zi * G.cpp;
@@ -350,6 +363,82 @@ __global__ void __launch_bounds__(256, 2) k_aa_odd_rows(SE<S> *__restrict__ f, S
             mom[4 * s + n1] = m.T.y;
         }
     }
+}
+
+template <int S, bool MOM>
+__global__ void __launch_bounds__(256, 2) k_aa_odd_rows(SE<S> *__restrict__ f, SE<S> *__restrict__ g, Geom G,
+                                                        Phys P, float *__restrict__ mom) {
+    k_aa_odd_rows_tile<S, MOM>(f, g, G, P, mom, blockIdx.x, threadIdx.x, blockDim.x);
+}
+
+// ------------------------------------------------- batched persistent launch ----
+//
+// Many independent cells advance in one launch.  The cells' tiles (a tile is
+// one block's share of one cell's step: a 512-node pair range of the even
+// step, a 512-node row chunk of the odd step, or a range of face nodes) are
+// listed per step parity; the blocks of a persistent grid stride over the
+// list and meet at a grid-wide barrier after every time step.  The launch is
+// cooperative, so all blocks are resident; the barrier still gives up after
+// a cycle budget and reports it instead of waiting forever.
+
+template <int S, int BS>
+__global__ void __launch_bounds__(BS, BS == 128 ? 3 : 1)
+    k_batch(const CellDev *__restrict__ cells, const Tile *__restrict__ even, int n_even, const Tile *__restrict__ odd,
+            int n_odd, int nsteps, int parity0, GridBarrier *bar, long long budget) {
+    // the current tile's cell description, staged in shared memory so that its
+    // fields are re-read cheaply instead of held in registers
+    __shared__ CellDev sc;
+    __shared__ Tile st;
+    for (int step = 0; step < nsteps; ++step) {
+        const bool odd_step = ((parity0 + step) & 1) != 0;
+        const Tile *tl = odd_step ? odd : even;
+        const int nt = odd_step ? n_odd : n_even;
+        for (int t = blockIdx.x; t < nt; t += gridDim.x) {
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                st = tl[t];
+                sc = cells[st.cell];
+            }
+            __syncthreads();
+            SE<S> *f = static_cast<SE<S> *>(sc.f);
+            SE<S> *g = static_cast<SE<S> *>(sc.g);
+            if (st.kind == TILE_EVEN)
+                k_aa_even2_tile<S, false>(f, g, sc.G, sc.P, nullptr, st.blk, threadIdx.x, BS);
+            else if (st.kind == TILE_ROWS)
+                k_aa_odd_rows_tile<S, false>(f, g, sc.G, sc.P, nullptr, st.blk, threadIdx.x, BS);
+            else
+                k_aa_odd_face_tile<S, false>(f, g, sc.G, sc.P, nullptr, sc.face, sc.nface, st.blk, threadIdx.x, BS);
+        }
+        if (!grid_barrier(bar, gridDim.x, budget)) return;
+    }
+}
+
+template <int S> static const void *batch_kernel(int block) {
+    return block == 128 ? reinterpret_cast<const void *>(&k_batch<S, 128>)
+                        : reinterpret_cast<const void *>(&k_batch<S, 256>);
+}
+
+const void *batch_kernel_ptr(int storage, int block) {
+    switch (storage) {
+    case ST_F32: return batch_kernel<ST_F32>(block);
+    case ST_F16: return batch_kernel<ST_F16>(block);
+    default: return batch_kernel<ST_BF16>(block);
+    }
+}
+
+cudaError_t launch_batch(int storage, const BatchArgs &a) {
+    void *args[] = {(void *)&a.cells, (void *)&a.even, (void *)&a.n_even, (void *)&a.odd, (void *)&a.n_odd,
+                    (void *)&a.nsteps, (void *)&a.parity0, (void *)&a.bar, (void *)&a.budget};
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(a.grid);
+    cfg.blockDim = dim3(a.block);
+    cfg.stream = a.stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, batch_kernel_ptr(storage, a.block), args);
 }
 
 // ------------------------------------------------------ two-buffer pull ----

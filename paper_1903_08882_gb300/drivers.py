@@ -1,0 +1,88 @@
+"""Run drivers over the C ABI: steady-state runs (Sec. 3), statistically
+averaged runs (Sec. 4) and the host-side formulas of the paper.
+
+These only sequence lbm_step / lbm_sample / lbm_diagnostics calls and do
+scalar arithmetic on the returned diagnostics; every lattice operation runs
+in the CUDA library.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+
+def free_fall_steps(H: float, U: float) -> float:
+    """Lattice steps per free-fall time t_f = sqrt(H/(g beta dT)) = H/U."""
+    return H / U
+
+
+def run_to_steady(lat, every: int = 1000, tol: float = 1e-7, max_steps: int = 2_000_000, face: int = 0,
+                  min_steps: int = 0):
+    """Advance until the relative change of the Nusselt number of Dirichlet
+    face `face` over `every` steps is below `tol` (the steady criterion on the
+    hot-wall Nusselt number; Sec. 3 uses a field criterion instead).
+    Returns dict(steps, converged, Nu, history, diag)."""
+    lat.sample()
+    prev = lat.diagnostics()["Nu_face"][face]
+    hist, steps = [prev], 0
+    while steps < max_steps:
+        lat.step(every)
+        steps += every
+        lat.sample()
+        d = lat.diagnostics(reset=True)
+        nu = d["Nu_face"][face]
+        hist.append(nu)
+        if steps >= min_steps and abs(nu - prev) <= tol * abs(nu):
+            return dict(steps=steps, converged=True, Nu=nu, history=np.array(hist), diag=d)
+        prev = nu
+    return dict(steps=steps, converged=False, Nu=prev, history=np.array(hist), diag=d)
+
+
+def field_residuals(u_new, u_old, T_new, T_old):
+    """Steady-state residuals of Sec. 3: sum |u(t+dt) - u(t)|_2 / sum |u(t)|_2
+    and sum |T(t+dt) - T(t)| / sum |T(t)| over the nodes."""
+    du = np.sqrt(((u_new - u_old) ** 2).sum(axis=0)).sum() / max(np.sqrt((u_old**2).sum(axis=0)).sum(), 1e-300)
+    dT = np.abs(T_new - T_old).sum() / max(np.abs(T_old).sum(), 1e-300)
+    return du, dT
+
+
+def averaged_statistics(lat, transient_steps: int, average_steps: int, diag_every: int):
+    """Sec. 4 protocol: discard a transient, then average the sampled
+    diagnostics over average_steps (samples every diag_every steps are taken
+    by the library when it was created with that diag_every).  Returns the
+    volume-and-time averages Re^rms, Re_w^rms, Nu_vol, Nu_wall, Nu_kin, Nu_th."""
+    lat.step(transient_steps)
+    lat.diagnostics(reset=True)
+    lat.step(average_steps)
+    d = lat.diagnostics(reset=False)
+    nu_wall = 0.5 * (d["avg_Nu_face"][4] - d["avg_Nu_face"][5])
+    return dict(Re_rms=d["avg_Re_rms"], Re_w=d["avg_Re_w"], Nu_vol=d["avg_Nu_vol"], Nu_wall=nu_wall,
+                Nu_kin=d["avg_Nu_kin"], Nu_th=d["avg_Nu_th"], E=d["avg_E"], samples=d["samples"], diag=d)
+
+
+def resolution(Ra: float, Pr: float, Nu: float, H: float):
+    """Resolution estimates of Sec. 4 (Table 5): Kolmogorov length
+    eta = H Pr^(1/2) / [Ra (Nu - 1)]^(1/4), Batchelor length eta_B = eta Pr^(-1/2),
+    Kolmogorov time tau_eta = sqrt(Pr/(Nu - 1)) in free-fall units, and the nodes
+    in the thermal boundary layer N_BL = H/(2 Nu); grid spacing 1, time step
+    U/H free-fall units (lattice units with U the free-fall velocity)."""
+    eta = H * math.sqrt(Pr) / (Ra * (Nu - 1.0)) ** 0.25
+    eta_B = eta / math.sqrt(Pr)
+    tau_eta = math.sqrt(Pr / (Nu - 1.0))
+    return dict(dg_over_eta=1.0 / eta, dg_over_etaB=1.0 / eta_B, tau_eta=tau_eta, N_BL=H / (2.0 * Nu))
+
+
+def centerline_probes(u3, U: float):
+    """Table 1 probes of the side-heated cell (hot wall at x = 0 here, so the
+    paper's y is our x): maximum horizontal velocity u along the vertical
+    centreline of the mid-plane y = 1/2, with its height z, and maximum
+    vertical velocity w along the horizontal centreline, with its position x.
+    Velocities in free-fall units; positions at node centres (j + 1/2)/N."""
+    nz, ny, nx = u3.shape[1:]
+    jy, jx, jz = ny // 2, nx // 2, nz // 2
+    col = u3[0][:, jy, jx] / U
+    row = u3[2][jz, jy, :] / U
+    k = int(np.argmax(np.abs(col)))
+    i = int(np.argmax(np.abs(row)))
+    return dict(u_max=float(col[k]), z=(k + 0.5) / nz, w_max=float(row[i]), x=(i + 0.5) / nx)

@@ -73,6 +73,13 @@ class LbmDiag(ctypes.Structure):
         return out
 
 
+class LbmSchedule(ctypes.Structure):
+    _fields_ = [("block_size", c_int), ("blocks_per_sm", c_int), ("steps_per_launch", c_int), ("graph_chunk", c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class LbmError(RuntimeError):
     def __init__(self, status: int, message: str, diag: dict | None = None):
         super().__init__(f"lbm status {status}: {message}")
@@ -112,6 +119,13 @@ def lib():
         "lbm_device_view": ([c_void_p, C, C, i64p, P(c_int)], c_int),
         "lbm_reduce_noalloc": ([c_void_p, c_int64, c_int, c_int, c_int, P(LbmWall), c_double, c_int, c_void_p,
                                 c_void_p], c_int),
+        "lbm_batch_create": ([P(c_void_p), c_int, c_void_p, C], c_int),
+        "lbm_batch_destroy": ([c_void_p], None),
+        "lbm_batch_step": ([c_void_p, c_int64], c_int),
+        "lbm_batch_get_schedule": ([c_void_p, P(LbmSchedule)], c_int),
+        "lbm_batch_set_schedule": ([c_void_p, P(LbmSchedule)], c_int),
+        "lbm_batch_autotune": ([c_void_p, c_int, P(LbmSchedule)], c_int),
+        "lbm_batch_set_barrier_budget": ([c_void_p, c_int64], c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -342,6 +356,99 @@ def lbm_reduce_noalloc(fields_ptr: int, stride: int, nx: int, ny: int, nz: int, 
     st = lib().lbm_reduce_noalloc(c_void_p(fields_ptr), int(stride), int(nx), int(ny), int(nz), w, float(a_T),
                                   int(blocks), c_void_p(sums_ptr), c_void_p(int(stream or 0) or None))
     _check(None, st)
+
+
+# ----------------------------------------------------------------- batches --
+
+def _bcheck(status):
+    if status != LBM_OK:
+        raise LbmError(status, lib().lbm_last_error(None).decode())
+
+
+def lbm_batch_create(ctxs, stream=None):
+    """Batch over existing contexts (ctypes handles).  stream: torch.cuda.Stream,
+    raw cudaStream_t int, or None for the current PyTorch stream."""
+    L = lib()
+    if stream is None:
+        import torch
+
+        stream = torch.cuda.current_stream().cuda_stream
+    elif hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    arr = (c_void_p * len(ctxs))(*[c.value for c in ctxs])
+    out = ctypes.c_void_p()
+    _bcheck(L.lbm_batch_create(arr, len(ctxs), c_void_p(int(stream) or None), ctypes.byref(out)))
+    return out
+
+
+def lbm_batch_destroy(batch):
+    lib().lbm_batch_destroy(batch)
+
+
+def lbm_batch_step(batch, n: int):
+    _bcheck(lib().lbm_batch_step(batch, int(n)))
+
+
+def lbm_batch_get_schedule(batch) -> dict:
+    s = LbmSchedule()
+    _bcheck(lib().lbm_batch_get_schedule(batch, ctypes.byref(s)))
+    return s.as_dict()
+
+
+def lbm_batch_set_schedule(batch, block_size=256, blocks_per_sm=1, steps_per_launch=100, graph_chunk=1000):
+    s = LbmSchedule(block_size, blocks_per_sm, steps_per_launch, graph_chunk)
+    _bcheck(lib().lbm_batch_set_schedule(batch, ctypes.byref(s)))
+
+
+def lbm_batch_autotune(batch, trial_steps=20) -> dict:
+    s = LbmSchedule()
+    _bcheck(lib().lbm_batch_autotune(batch, int(trial_steps), ctypes.byref(s)))
+    return s.as_dict()
+
+
+def lbm_batch_set_barrier_budget(batch, cycles: int):
+    _bcheck(lib().lbm_batch_set_barrier_budget(batch, int(cycles)))
+
+
+class Batch:
+    """Owns a batch over Lattice objects (which must outlive it)."""
+
+    def __init__(self, lattices, stream=None):
+        self.lattices = list(lattices)
+        self.handle = lbm_batch_create([l.ctx for l in self.lattices], stream=stream)
+
+    def close(self):
+        if self.handle is not None and self.handle.value:
+            lbm_batch_destroy(self.handle)
+        self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def step(self, n):
+        lbm_batch_step(self.handle, n)
+
+    schedule = property(lambda self: lbm_batch_get_schedule(self.handle))
+
+    def set_schedule(self, **kw):
+        cur = self.schedule
+        cur.update(kw)
+        lbm_batch_set_schedule(self.handle, **cur)
+
+    def autotune(self, trial_steps=20):
+        return lbm_batch_autotune(self.handle, trial_steps)
+
+    def set_barrier_budget(self, cycles):
+        lbm_batch_set_barrier_budget(self.handle, cycles)
 
 
 class Lattice:

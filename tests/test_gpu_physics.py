@@ -1,0 +1,74 @@
+"""Long runs on the GPU against stored FP64-oracle results.
+
+Steady side-heated cell (Sec. 3): the hot- and cold-wall Nusselt numbers of
+the steady state against the oracle's steady state, within 0.1% (FP32
+storage) and 0.5% (FP16 storage).
+Rayleigh-Benard cell (Sec. 4): volume-and-time averages after the same
+transient and over the same window and sample points as the oracle, within
+2% (the flows need not follow the same trajectory).
+The stored values come from the oracle-only scripts next to them in
+tests/golden/; a test is skipped while its file is absent."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_1903_08882_gb300 import drivers, inputs
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    path = os.path.join(GOLDEN, name)
+    if not os.path.exists(path) or os.path.getsize(path) == 0:
+        pytest.skip(f"{name} not generated")
+    with open(path) as fh:
+        return json.load(fh)
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1903_08882_gb300 import _build
+    from paper_1903_08882_gb300 import lbm as L
+
+    _build.build()
+    return L
+
+
+@pytest.mark.parametrize("N", [33, 65])
+@pytest.mark.parametrize("storage,tol", [("fp32", 1e-3), ("fp16s", 5e-3)])
+def test_steady_side_heated_nusselt(lbm, N, storage, tol):
+    ref = _golden(f"steady_side_heated_{N}.json")
+    assert ref.get("converged", False)
+    with lbm.Lattice(N, N, N, lbm.walls_side_heated(), Ra=1e6, Pr=0.71, U=0.1, storage=storage) as lat:
+        r = drivers.run_to_steady(lat, every=1000, tol=1e-7, max_steps=400_000)
+        d = r["diag"]
+    if storage == "fp32":
+        assert r["converged"], r["steps"]
+    nu_hot, nu_cold = d["Nu_face"][0], -d["Nu_face"][1]
+    assert abs(nu_hot - ref["Nu_hot"]) <= tol * ref["Nu_hot"], (nu_hot, ref["Nu_hot"])
+    assert abs(nu_cold - ref["Nu_cold"]) <= tol * ref["Nu_cold"], (nu_cold, ref["Nu_cold"])
+    assert abs(d["Nu_link"][0] - ref["Nu_hot_link"]) <= tol * ref["Nu_hot_link"]
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16s"])
+def test_rayleigh_benard_statistics(lbm, storage):
+    ref = _golden("rb_statistics_32_Ra1e6_Pr7.json")
+    N, every = ref["N"], ref["sample_every"]
+    with lbm.Lattice(N, N, N, lbm.walls_rayleigh_benard(), Ra=ref["Ra"], Pr=ref["Pr"], U=ref["U"],
+                     storage=storage, diag_every=every) as lat:
+        lat.set_fields(1.0, np.zeros(3), inputs.rb_initial_temperature(N, N, N, seed=ref["seed"]))
+        s = drivers.averaged_statistics(lat, ref["transient_steps"], ref["average_steps"], every)
+    assert s["samples"] == ref["samples"]
+    for k in ("Nu_vol", "Nu_wall", "Nu_kin", "Nu_th", "Re_rms", "Re_w"):
+        assert abs(s[k] - ref[k]) <= 0.02 * abs(ref[k]), (k, s[k], ref[k])
+    # the four Nusselt numbers of Sec. 4 describe one heat flux
+    nus = np.array([s["Nu_vol"], s["Nu_wall"], s["Nu_kin"], s["Nu_th"]])
+    assert nus.std() / nus.mean() < 0.1, nus
