@@ -286,6 +286,49 @@ def _e2e(lbm, lat, args, stream, dist):
             "h2d_bytes_per_step": 5 * 4 * N ** 3, "d2h_bytes_per_step": 8 * (2 * 24 + 1)}
 
 
+def bench_batched(lbm, args, stream):
+    """Batched sweep: 64 cells (edges 33-97, Ra 1e4-1e7, Pr 0.71/7, half side-
+    heated, half Rayleigh-Benard) advanced by one persistent launch per run of
+    steps, replayed as 1000-step CUDA graphs with an autotuned schedule, against
+    the same cells advanced one launch (pair) per cell per step."""
+    import torch
+
+    from paper_1903_08882_gb300 import drivers
+
+    lats, draws = drivers.sweep_cells(lbm, stream=stream)
+    nodes = sum(d["edge"] ** 3 for d in draws)
+    chunk = 1000
+    res = {"cells": len(lats), "nodes": nodes, "edges": sorted({d["edge"] for d in draws})}
+    try:
+        with lbm.Batch(lats, stream=stream) as b:
+            best = b.autotune(trial_steps=20)
+            b.set_schedule(steps_per_launch=100, graph_chunk=chunk)
+            b.step(chunk)  # capture + warm-up
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            k = max(1, args.steps // 3)
+            ev0.record(stream)
+            b.step(k * chunk)
+            ev1.record(stream)
+            ev1.synchronize()
+            t_b = ev0.elapsed_time(ev1) / 1e3
+            res["schedule"] = b.schedule
+        ev0.record(stream)
+        for lat in lats:
+            lat.step(chunk)
+        ev1.record(stream)
+        ev1.synchronize()
+        t_s = ev0.elapsed_time(ev1) / 1e3
+        res["glups_batched"] = round(nodes * chunk * k / t_b / 1e9, 3)
+        res["glups_one_launch_per_cell"] = round(nodes * chunk / t_s / 1e9, 3)
+        res["speedup"] = round(res["glups_batched"] / res["glups_one_launch_per_cell"], 3)
+        res["graph_chunk_steps"] = chunk
+        res["autotuned"] = best
+    finally:
+        for lat in lats:
+            lat.close()
+    return res
+
+
 def run_gpu(args):
     import torch
 
@@ -324,6 +367,10 @@ def run_gpu(args):
                 "kernel_ms": round(r["kernel_seconds"] * 1e3, 4),
                 "kernel_glups": round(nodes / r["kernel_seconds"] / 1e9, 3)}
 
+    batched = None
+    if not args.no_batch and ws == 1:
+        with torch.cuda.stream(stream):
+            batched = bench_batched(lbm, args, stream)
     cpu_rate, threads, sample = _cpu_oracle_rate() if not args.no_cpu else (None, None, None)
     line = {
         "metric": METRIC, "value": round(main["glups"], 3), "unit": "GLUPS", "n_gpus": ws,
@@ -347,6 +394,7 @@ def run_gpu(args):
                                   "speedup_vs_fp32": round(r["glups"] / main["glups"], 3)}
                              for st, r in results.items() if st != "fp32"},
         "Nu_hot_after_run": main["Nu_hot"],
+        "batched_sweep": batched,
     }
     print(json.dumps(line), flush=True)
 
@@ -360,6 +408,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fp32-only", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-cell batched sweep")
     ap.add_argument("--edge", type=int, default=N_EDGE, help="cube edge; other than 257 only for profiling")
     ap.add_argument("--only", default=None, choices=["fp32", "fp16s", "bf16s"],
                     help="time one storage form only (profiling)")

@@ -86,3 +86,34 @@ def centerline_probes(u3, U: float):
     k = int(np.argmax(np.abs(col)))
     i = int(np.argmax(np.abs(row)))
     return dict(u_max=float(col[k]), z=(k + 0.5) / nz, w_max=float(row[i]), x=(i + 0.5) / nx)
+
+
+def sweep_cells(lbm, seed: int = 190308882, ncells: int = 64, storage: str = "fp32", stream=None,
+                min_bl_nodes: float = 2.0):
+    """Cells of a batched sweep: half side-heated, half Rayleigh-Benard, drawn
+    from inputs.cell_candidates.  A draw is skipped when the library rejects
+    its parameters (for instance a_T >= 1, a negative D3Q7 rest weight) or when
+    fewer than `min_bl_nodes` nodes would fall in the thermal boundary layer
+    H/(2 Nu), Nu estimated from the fit Nu = 0.153 Ra^0.289 of Sec. 4.
+    Returns (lattices, draws) with the lattices at rest."""
+    from . import inputs
+
+    lats, draws = [], []
+    for edge, Ra, Pr in inputs.cell_candidates(seed, 50 * ncells):
+        if len(lats) == ncells:
+            break
+        if edge / (2.0 * 0.153 * Ra ** 0.289) < min_bl_nodes:
+            continue
+        kind = "side" if len(lats) < ncells // 2 else "rb"
+        walls = lbm.walls_side_heated() if kind == "side" else lbm.walls_rayleigh_benard()
+        try:
+            lat = lbm.Lattice(edge, edge, edge, walls, Ra=Ra, Pr=Pr, storage=storage, stream=stream)
+        except lbm.LbmError as e:
+            if e.status == lbm.LBM_ERR_PARAM:
+                continue
+            raise
+        lats.append(lat)
+        draws.append(dict(edge=edge, Ra=Ra, Pr=Pr, kind=kind))
+    if len(lats) < ncells:
+        raise RuntimeError(f"only {len(lats)} usable cells drawn")
+    return lats, draws

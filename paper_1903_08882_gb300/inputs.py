@@ -58,3 +58,18 @@ def rb_initial_temperature(nx: int, ny: int, nz: int, seed: int, delta: float = 
     base = 0.5 - (k + 0.5) / nz
     T = np.broadcast_to(base[:, None, None], (nz, ny, nx)).copy()
     return T + noise((nz, ny, nx), seed, 11, delta)
+
+
+def cell_candidates(seed: int, count: int, edges=(33, 49, 65, 81, 97)):
+    """A seeded stream of cell draws for a batched sweep: edge length drawn
+    from `edges`, Ra log-uniform in [1e4, 1e7], Pr from {0.71, 7}.  Returns
+    a list of (edge, Ra, Pr) tuples; callers skip draws they cannot use."""
+    k = np.arange(count, dtype=np.uint64)
+    e = uniform(seed, 31, k)
+    r = uniform(seed, 32, k)
+    p = uniform(seed, 33, k)
+    out = []
+    for i in range(count):
+        edge = edges[min(int(e[i] * len(edges)), len(edges) - 1)]
+        out.append((edge, float(10.0 ** (4.0 + 3.0 * r[i])), 0.71 if p[i] < 0.5 else 7.0))
+    return out
