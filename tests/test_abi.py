@@ -18,9 +18,11 @@ def L():
     return lbm
 
 
-def _declared():
+def _declared(header=None):
     names = set()
     for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        if header and os.path.basename(h) != header:
+            continue
         src = open(h).read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
         names |= set(re.findall(r"\b(lbm_[a-z0-9_]+)\s*\(", src))
@@ -41,8 +43,11 @@ def test_library_exports_every_declared_symbol(L):
 
 
 def test_binding_covers_every_declared_symbol(L):
-    for n in _declared():
+    from paper_1903_08882_gb300 import unet
+
+    for n in _declared("lbm.h"):
         assert hasattr(L, n), n
+    assert _declared("lbm_nn.h") == set(unet.NN_SIGNATURES)
 
 
 def _status(L, p):
