@@ -36,7 +36,7 @@ sys.path.insert(0, ROOT)
 N_EDGE = 257
 RA, PR, U = 1e7, 0.71, 0.1
 CHUNK = 100                  # LB time steps per benchmark step
-BYTES_PER_NODE = {"fp32": 208, "fp16s": 104, "bf16s": 104}  # 26 populations read + written
+BYTES_PER_NODE = {"fp32": 208, "fp16s": 104, "bf16s": 104, "fp16m": 132}  # 26 populations read + written
 NOMINAL_HBM_GBS = 8000.0
 FALLBACK_HBM_GBS = 6800.0
 METRIC = "GLUPS (D3Q19+D3Q7) and % HBM roofline at 257^3, FP32 vs FP16 storage"
@@ -340,7 +340,7 @@ def run_gpu(args):
         _build.build()
     stream = torch.cuda.Stream()
     peak, peak_kind = _peak_hbm()
-    storages = ["fp32"] if args.fp32_only else ["fp32", "fp16s", "bf16s"]
+    storages = ["fp32"] if args.fp32_only else ["fp32", "fp16s", "bf16s", "fp16m"]
     if args.only:
         storages = [args.only]
     results = {}
@@ -410,7 +410,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-cell batched sweep")
     ap.add_argument("--edge", type=int, default=N_EDGE, help="cube edge; other than 257 only for profiling")
-    ap.add_argument("--only", default=None, choices=["fp32", "fp16s", "bf16s"],
+    ap.add_argument("--only", default=None, choices=["fp32", "fp16s", "bf16s", "fp16m"],
                     help="time one storage form only (profiling)")
     ap.add_argument("--npt", type=int, default=0, help="nodes per thread of the AA kernels (0: library default)")
     args = ap.parse_args()

@@ -57,9 +57,10 @@ typedef enum {
 } lbm_wall_kind;
 
 typedef enum {
-    LBM_FP32 = 0,  /* 4 bytes per population, 104 B per node   */
-    LBM_FP16S = 1, /* IEEE half deviations, 52 B per node       */
-    LBM_BF16S = 2  /* bfloat16 deviations, 52 B per node        */
+    LBM_FP32 = 0,  /* 4 bytes per population, 104 B per node                      */
+    LBM_FP16S = 1, /* IEEE half deviations, 52 B per node                          */
+    LBM_BF16S = 2, /* bfloat16 deviations, 52 B per node                           */
+    LBM_FP16M = 3  /* f as IEEE half deviations, g in FP32: 66 B per node          */
 } lbm_storage;
 
 typedef enum {
@@ -216,7 +217,8 @@ lbm_status lbm_load(lbm_ctx *ctx, const char *path);
 
 /* Device view of the population storage, for callers that keep data on the
  * GPU: base pointers of f (19 arrays) and g (7 arrays), elements between
- * consecutive population arrays, and the element size in bytes.  The layout
+ * consecutive population arrays, and the element size in bytes of f (g uses
+ * 4 bytes with LBM_FP16M, else the size of f).  The layout
  * of the values depends on the streaming scheme and on the step parity; use
  * lbm_get_populations to read them in a defined layout. */
 lbm_status lbm_device_view(lbm_ctx *ctx, void **f, void **g, int64_t *stride, int *elem_bytes);

@@ -45,7 +45,8 @@ struct lbm_ctx {
     size_t face_bytes = 0;
     uint32_t nface = 0;
     int nblocks = 0;
-    int elem = 4;
+    int elem = 4;   // bytes per flow population (f)
+    int elem_g = 4; // bytes per thermal population (g)
     int parity = 0;        // AA: 0 natural (next step even), 1 reversed
     int64_t step = 0;
     int64_t sample_step = -1;
@@ -80,7 +81,7 @@ struct lbm_ctx {
     double *acc() { return dsum + (size_t)nblocks * kNDiag + kNDiag; }
     void *fbase(int which) { return which ? pop2 : pop; }
     void *gbase(int which) {
-        return static_cast<char *>(which ? pop2 : pop) + (size_t)19 * G.stride * elem;
+        return static_cast<char *>(which ? pop2 : pop) + (size_t)19 * G.stride * elem;  // g follows the 19 f arrays
     }
     int layout() const { return p.streaming == LBM_STREAM_PULL2 ? 2 : (parity ? 1 : 0); }
 };
@@ -150,7 +151,7 @@ lbm_status validate_and_derive(const lbm_params &p, lbm_constants &c, std::strin
             return LBM_ERR_PARAM;
         }
     }
-    if (p.storage < 0 || p.storage > 2 || p.streaming < 0 || p.streaming > 1) {
+    if (p.storage < 0 || p.storage > 3 || p.streaming < 0 || p.streaming > 1) {
         why = "unknown storage or streaming scheme";
         return LBM_ERR_PARAM;
     }
@@ -308,6 +309,7 @@ lbm_status lbm_create(const lbm_params *params, const lbm_allocator *alloc, void
     }
     ctx->block = params->block_size ? params->block_size : 256;
     ctx->elem = params->storage == LBM_FP32 ? 4 : 2;
+    ctx->elem_g = (params->storage == LBM_FP32 || params->storage == LBM_FP16M) ? 4 : 2;
 
     Geom &G = ctx->G;
     G.nx = params->nx;
@@ -351,7 +353,7 @@ lbm_status lbm_create(const lbm_params *params, const lbm_allocator *alloc, void
         if (dir) P.dir_mask |= 1 << f;
     }
 
-    ctx->pop_bytes = (size_t)26 * G.stride * ctx->elem;
+    ctx->pop_bytes = (size_t)G.stride * (19 * (size_t)ctx->elem + 7 * (size_t)ctx->elem_g);
     ctx->mom_bytes = (size_t)kMomArrays * G.stride * sizeof(float);
     ctx->nblocks = diag_blocks(G);
     ctx->dsum_bytes = ((size_t)ctx->nblocks * kNDiag + 2 * kNDiag + 1) * sizeof(double);

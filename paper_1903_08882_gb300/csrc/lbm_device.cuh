@@ -56,7 +56,12 @@ __host__ __device__ constexpr float w19(int i) {
 
 // -------------------------------------------------------- storage types ----
 
-enum StorageKind { ST_F32 = 0, ST_F16 = 1, ST_BF16 = 2 };
+enum StorageKind { ST_F32 = 0, ST_F16 = 1, ST_BF16 = 2, ST_F16M = 3 };
+
+// Element format of the flow (f) and thermal (g) arrays of a storage kind:
+// ST_F16M keeps f in FP16 and g in FP32.
+__host__ __device__ constexpr int FS(int S) { return S == ST_F16M ? ST_F16 : S; }
+__host__ __device__ constexpr int GS(int S) { return S == ST_F16M ? ST_F32 : S; }
 
 template <int S> struct Store;
 template <> struct Store<ST_F32> {

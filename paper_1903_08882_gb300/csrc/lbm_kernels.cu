@@ -25,7 +25,8 @@ namespace lbm {
 
 enum Layout { LAYOUT_NATURAL = 0, LAYOUT_REVERSED = 1, LAYOUT_PULL = 2 };
 
-template <int S> using SE = typename Store<S>::T;
+template <int S> using SEF = typename Store<FS(S)>::T; // flow element type
+template <int S> using SEG = typename Store<GS(S)>::T; // thermal element type
 
 // Hide a pointer's value from the compiler so that addresses computed from it
 // before the collision are not kept live across it (recomputing 26 addresses
@@ -37,15 +38,15 @@ template <typename T> __device__ __forceinline__ T *opaque(T *p) {
 
 // Read the pre-collision populations of node (x, y, z) from a device layout.
 template <int S>
-__device__ __forceinline__ void read_natural(const SE<S> *__restrict__ f, const SE<S> *__restrict__ g,
+__device__ __forceinline__ void read_natural(const SEF<S> *__restrict__ f, const SEG<S> *__restrict__ g,
                                              const Geom &G, const Phys &P, int layout, uint32_t n,
                                              int x, int y, int z, float (&fl)[19], float (&gl)[7]) {
     const int64_t s = G.stride;
     if (layout == LAYOUT_NATURAL) {
 #pragma unroll
-        for (int i = 0; i < 19; ++i) fl[i] = Store<S>::ld(f + i * s + n);
+        for (int i = 0; i < 19; ++i) fl[i] = Store<FS(S)>::ld(f + i * s + n);
 #pragma unroll
-        for (int i = 0; i < 7; ++i) gl[i] = Store<S>::ld(g + i * s + n);
+        for (int i = 0; i < 7; ++i) gl[i] = Store<GS(S)>::ld(g + i * s + n);
         return;
     }
     const Nbr b = neighbours(G, x, y, z);
@@ -54,18 +55,18 @@ __device__ __forceinline__ void read_natural(const SE<S> *__restrict__ f, const 
     for (int i = 0; i < 19; ++i) {
         const int slot_in = rev ? opp19(i) : i, slot_wall = rev ? i : opp19(i);
         if (!src_wall(b, ex19(i), ey19(i), ez19(i)))
-            fl[i] = Store<S>::ld(f + slot_in * s + (int64_t)n + src_off(b, ex19(i), ey19(i), ez19(i)));
+            fl[i] = Store<FS(S)>::ld(f + slot_in * s + (int64_t)n + src_off(b, ex19(i), ey19(i), ez19(i)));
         else
-            fl[i] = Store<S>::ld(f + slot_wall * s + n);
+            fl[i] = Store<FS(S)>::ld(f + slot_wall * s + n);
     }
 #pragma unroll
     for (int i = 0; i < 7; ++i) {
         const int slot_in = rev ? opp7(i) : i, slot_wall = rev ? i : opp7(i);
         if (!src_wall(b, ex7(i), ey7(i), ez7(i))) {
-            gl[i] = Store<S>::ld(g + slot_in * s + (int64_t)n + src_off(b, ex7(i), ey7(i), ez7(i)));
+            gl[i] = Store<GS(S)>::ld(g + slot_in * s + (int64_t)n + src_off(b, ex7(i), ey7(i), ez7(i)));
         } else {
             const int fc = face_of(-ex7(i), -ey7(i), -ez7(i));
-            const float v = Store<S>::ld(g + slot_wall * s + n);
+            const float v = Store<GS(S)>::ld(g + slot_wall * s + n);
             gl[i] = ((P.dir_mask >> fc) & 1) ? P.abbT[fc] - v : v;
         }
     }
@@ -93,16 +94,16 @@ __device__ __forceinline__ void write_sample(float *__restrict__ mom, int64_t s,
 
 // Even step: natural -> reversed.  Reads and writes only the node's own slots.
 template <int S, bool MOM>
-__global__ void __launch_bounds__(256, 3) k_aa_even(SE<S> *__restrict__ f, SE<S> *__restrict__ g, Geom G,
+__global__ void __launch_bounds__(256, 3) k_aa_even(SEF<S> *__restrict__ f, SEG<S> *__restrict__ g, Geom G,
                                                  Phys P, float *__restrict__ mom) {
     const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= G.n) return;
     const int64_t s = G.stride;
     float fl[19], gl[7];
 #pragma unroll
-    for (int i = 0; i < 19; ++i) fl[i] = Store<S>::ld(f + i * s + n);
+    for (int i = 0; i < 19; ++i) fl[i] = Store<FS(S)>::ld(f + i * s + n);
 #pragma unroll
-    for (int i = 0; i < 7; ++i) gl[i] = Store<S>::ld(g + i * s + n);
+    for (int i = 0; i < 7; ++i) gl[i] = Store<GS(S)>::ld(g + i * s + n);
     float g0[7];
 #pragma unroll
     for (int i = 0; i < 7; ++i) g0[i] = gl[i];
@@ -110,9 +111,9 @@ __global__ void __launch_bounds__(256, 3) k_aa_even(SE<S> *__restrict__ f, SE<S>
     f = opaque(f);
     g = opaque(g);
 #pragma unroll
-    for (int i = 0; i < 19; ++i) Store<S>::st(f + opp19(i) * s + n, fl[i]);
+    for (int i = 0; i < 19; ++i) Store<FS(S)>::st(f + opp19(i) * s + n, fl[i]);
 #pragma unroll
-    for (int i = 0; i < 7; ++i) Store<S>::st(g + opp7(i) * s + n, gl[i]);
+    for (int i = 0; i < 7; ++i) Store<GS(S)>::st(g + opp7(i) * s + n, gl[i]);
     if (MOM) {
         int x, y, z;
         node_xyz(G, n, x, y, z);
@@ -128,7 +129,7 @@ __global__ void __launch_bounds__(256, 3) k_aa_even(SE<S> *__restrict__ f, SE<S>
 // take the uniform offsets e_i of the flat index; nodes next to a face go
 // through the general path with wrap-around and wall rules.
 template <int S, bool MOM>
-__global__ void __launch_bounds__(256, 3) k_aa_odd_interior(SE<S> *__restrict__ f, SE<S> *__restrict__ g,
+__global__ void __launch_bounds__(256, 3) k_aa_odd_interior(SEF<S> *__restrict__ f, SEG<S> *__restrict__ g,
                                                             Geom G, Phys P, float *__restrict__ mom) {
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= G.ni) return;
@@ -139,21 +140,21 @@ __global__ void __launch_bounds__(256, 3) k_aa_odd_interior(SE<S> *__restrict__ 
     const uint32_t n = (xi + 1) + static_cast<uint32_t>(G.nx) * ((yi + 1) + static_cast<uint32_t>(G.ny) * (zi + 1));
     const int64_t s = G.stride;
     float fl[19], gl[7];
-    fl[0] = Store<S>::ld(f + n);
+    fl[0] = Store<FS(S)>::ld(f + n);
 #pragma unroll
-    for (int i = 1; i < 19; ++i) fl[i] = Store<S>::ld(f + opp19(i) * s + (int64_t)(n - G.off[i]));
-    gl[0] = Store<S>::ld(g + n);
+    for (int i = 1; i < 19; ++i) fl[i] = Store<FS(S)>::ld(f + opp19(i) * s + (int64_t)(n - G.off[i]));
+    gl[0] = Store<GS(S)>::ld(g + n);
 #pragma unroll
-    for (int i = 1; i < 7; ++i) gl[i] = Store<S>::ld(g + opp7(i) * s + (int64_t)(n - G.off[i]));
+    for (int i = 1; i < 7; ++i) gl[i] = Store<GS(S)>::ld(g + opp7(i) * s + (int64_t)(n - G.off[i]));
     const Macro m = collide(P, fl, gl);
     f = opaque(f);
     g = opaque(g);
-    Store<S>::st(f + n, fl[0]);
+    Store<FS(S)>::st(f + n, fl[0]);
 #pragma unroll
-    for (int i = 1; i < 19; ++i) Store<S>::st(f + i * s + (int64_t)(n + G.off[i]), fl[i]);
-    Store<S>::st(g + n, gl[0]);
+    for (int i = 1; i < 19; ++i) Store<FS(S)>::st(f + i * s + (int64_t)(n + G.off[i]), fl[i]);
+    Store<GS(S)>::st(g + n, gl[0]);
 #pragma unroll
-    for (int i = 1; i < 7; ++i) Store<S>::st(g + i * s + (int64_t)(n + G.off[i]), gl[i]);
+    for (int i = 1; i < 7; ++i) Store<GS(S)>::st(g + i * s + (int64_t)(n + G.off[i]), gl[i]);
     if (MOM) {
         mom[n] = m.drho;
         mom[s + n] = m.u;
@@ -165,7 +166,7 @@ __global__ void __launch_bounds__(256, 3) k_aa_odd_interior(SE<S> *__restrict__ 
 
 // Nodes next to a face, listed in `list`.
 template <int S, bool MOM>
-__device__ __forceinline__ void k_aa_odd_face_tile(SE<S> *__restrict__ f, SE<S> *__restrict__ g, const Geom &G,
+__device__ __forceinline__ void k_aa_odd_face_tile(SEF<S> *__restrict__ f, SEG<S> *__restrict__ g, const Geom &G,
                                                         const Phys &P, float *__restrict__ mom,
                                                         const uint32_t *__restrict__ list, uint32_t count, uint32_t blk, uint32_t tid, uint32_t bdim) {
     const uint32_t t = blk * bdim + tid;
@@ -179,17 +180,17 @@ __device__ __forceinline__ void k_aa_odd_face_tile(SE<S> *__restrict__ f, SE<S> 
 #pragma unroll
     for (int i = 0; i < 19; ++i) {
         if (!src_wall(b, ex19(i), ey19(i), ez19(i)))
-            fl[i] = Store<S>::ld(f + opp19(i) * s + (int64_t)n + src_off(b, ex19(i), ey19(i), ez19(i)));
+            fl[i] = Store<FS(S)>::ld(f + opp19(i) * s + (int64_t)n + src_off(b, ex19(i), ey19(i), ez19(i)));
         else
-            fl[i] = Store<S>::ld(f + i * s + n);
+            fl[i] = Store<FS(S)>::ld(f + i * s + n);
     }
 #pragma unroll
     for (int i = 0; i < 7; ++i) {
         if (!src_wall(b, ex7(i), ey7(i), ez7(i))) {
-            gl[i] = Store<S>::ld(g + opp7(i) * s + (int64_t)n + src_off(b, ex7(i), ey7(i), ez7(i)));
+            gl[i] = Store<GS(S)>::ld(g + opp7(i) * s + (int64_t)n + src_off(b, ex7(i), ey7(i), ez7(i)));
         } else {
             const int fc = face_of(-ex7(i), -ey7(i), -ez7(i));
-            const float v = Store<S>::ld(g + i * s + n);
+            const float v = Store<GS(S)>::ld(g + i * s + n);
             gl[i] = ((P.dir_mask >> fc) & 1) ? P.abbT[fc] - v : v;
         }
     }
@@ -202,25 +203,25 @@ __device__ __forceinline__ void k_aa_odd_face_tile(SE<S> *__restrict__ f, SE<S> 
 #pragma unroll
     for (int i = 0; i < 19; ++i) {
         if (!dst_wall(b, ex19(i), ey19(i), ez19(i)))
-            Store<S>::st(f + i * s + (int64_t)n + dst_off(b, ex19(i), ey19(i), ez19(i)), fl[i]);
+            Store<FS(S)>::st(f + i * s + (int64_t)n + dst_off(b, ex19(i), ey19(i), ez19(i)), fl[i]);
         else
-            Store<S>::st(f + opp19(i) * s + n, fl[i]);
+            Store<FS(S)>::st(f + opp19(i) * s + n, fl[i]);
     }
 #pragma unroll
     for (int i = 0; i < 7; ++i) {
         if (!dst_wall(b, ex7(i), ey7(i), ez7(i))) {
-            Store<S>::st(g + i * s + (int64_t)n + dst_off(b, ex7(i), ey7(i), ez7(i)), gl[i]);
+            Store<GS(S)>::st(g + i * s + (int64_t)n + dst_off(b, ex7(i), ey7(i), ez7(i)), gl[i]);
         } else {
             const int fc = face_of(ex7(i), ey7(i), ez7(i));
             const float v = gl[i];
-            Store<S>::st(g + opp7(i) * s + n, ((P.dir_mask >> fc) & 1) ? P.abbT[fc] - v : v);
+            Store<GS(S)>::st(g + opp7(i) * s + n, ((P.dir_mask >> fc) & 1) ? P.abbT[fc] - v : v);
         }
     }
     if (MOM) write_sample(mom, s, n, m, b, g0);
 }
 
 template <int S, bool MOM>
-__global__ void __launch_bounds__(256, 3) k_aa_odd_face(SE<S> *__restrict__ f, SE<S> *__restrict__ g, Geom G,
+__global__ void __launch_bounds__(256, 3) k_aa_odd_face(SEF<S> *__restrict__ f, SEG<S> *__restrict__ g, Geom G,
                                                         Phys P, float *__restrict__ mom,
                                                         const uint32_t *__restrict__ list, uint32_t count) {
     k_aa_odd_face_tile<S, MOM>(f, g, G, P, mom, list, count, blockIdx.x, threadIdx.x, blockDim.x);
@@ -235,16 +236,16 @@ __global__ void __launch_bounds__(256, 3) k_aa_odd_face(SE<S> *__restrict__ f, S
 // element, which no real node ever reads).
 
 template <int S, bool MOM>
-__device__ __forceinline__ void k_aa_even2_tile(SE<S> *__restrict__ f, SE<S> *__restrict__ g, const Geom &G,
+__device__ __forceinline__ void k_aa_even2_tile(SEF<S> *__restrict__ f, SEG<S> *__restrict__ g, const Geom &G,
                                                      const Phys &P, float *__restrict__ mom, uint32_t blk, uint32_t tid, uint32_t bdim) {
     const uint32_t n = 2u * (blk * bdim + tid);
     if (n >= G.n) return;
     const int64_t s = G.stride;
     float2 fl[19], gl[7];
 #pragma unroll
-    for (int i = 0; i < 19; ++i) fl[i] = Store2<S>::ld(f + i * s + n);
+    for (int i = 0; i < 19; ++i) fl[i] = Store2<FS(S)>::ld(f + i * s + n);
 #pragma unroll
-    for (int i = 0; i < 7; ++i) gl[i] = Store2<S>::ld(g + i * s + n);
+    for (int i = 0; i < 7; ++i) gl[i] = Store2<GS(S)>::ld(g + i * s + n);
     float2 g0[7];
 #pragma unroll
     for (int i = 0; i < 7; ++i) g0[i] = gl[i];
@@ -252,9 +253,9 @@ __device__ __forceinline__ void k_aa_even2_tile(SE<S> *__restrict__ f, SE<S> *__
     f = opaque(f);
     g = opaque(g);
 #pragma unroll
-    for (int i = 0; i < 19; ++i) Store2<S>::st(f + opp19(i) * s + n, fl[i]);
+    for (int i = 0; i < 19; ++i) Store2<FS(S)>::st(f + opp19(i) * s + n, fl[i]);
 #pragma unroll
-    for (int i = 0; i < 7; ++i) Store2<S>::st(g + opp7(i) * s + n, gl[i]);
+    for (int i = 0; i < 7; ++i) Store2<GS(S)>::st(g + opp7(i) * s + n, gl[i]);
     if (MOM) {
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
@@ -277,7 +278,7 @@ __device__ __forceinline__ void k_aa_even2_tile(SE<S> *__restrict__ f, SE<S> *__
 }
 
 template <int S, bool MOM>
-__global__ void __launch_bounds__(256, 2) k_aa_even2(SE<S> *__restrict__ f, SE<S> *__restrict__ g, Geom G,
+__global__ void __launch_bounds__(256, 2) k_aa_even2(SEF<S> *__restrict__ f, SEG<S> *__restrict__ g, Geom G,
                                                      Phys P, float *__restrict__ mom) {
     k_aa_even2_tile<S, MOM>(f, g, G, P, mom, blockIdx.x, threadIdx.x, blockDim.x);
 }
@@ -297,7 +298,7 @@ __device__ __forceinline__ uint32_t interior_node(const Geom &G, uint32_t t) {
 // at x = 0 or x = nx-1 (and lanes past the end of the run) are left to the
 // face kernel: their loads stay in bounds and their results are not stored.
 template <int S, bool MOM>
-__device__ __forceinline__ void k_aa_odd_rows_tile(SE<S> *__restrict__ f, SE<S> *__restrict__ g, const Geom &G,
+__device__ __forceinline__ void k_aa_odd_rows_tile(SEF<S> *__restrict__ f, SEG<S> *__restrict__ g, const Geom &G,
                                                         const Phys &P, float *__restrict__ mom, uint32_t blk, uint32_t tid, uint32_t bdim) {
     const uint32_t warp = blk * (bdim >> 5) + (tid >> 5);
     const uint32_t lane = tid & 31u;
@@ -315,36 +316,36 @@ __device__ __forceinline__ void k_aa_odd_rows_tile(SE<S> *__restrict__ f, SE<S> 
     if (!a0 && !a1) return;
     const int64_t s = G.stride;
     float2 fl[19], gl[7];
-    fl[0] = make_float2(Store<S>::ld(f + n0), Store<S>::ld(f + n0 + 32));
+    fl[0] = make_float2(Store<FS(S)>::ld(f + n0), Store<FS(S)>::ld(f + n0 + 32));
 #pragma unroll
     for (int i = 1; i < 19; ++i) {
-        const SE<S> *q = f + opp19(i) * s + (int64_t)(n0 - G.off[i]);
-        fl[i] = make_float2(Store<S>::ld(q), Store<S>::ld(q + 32));
+        const SEF<S> *q = f + opp19(i) * s + (int64_t)(n0 - G.off[i]);
+        fl[i] = make_float2(Store<FS(S)>::ld(q), Store<FS(S)>::ld(q + 32));
     }
-    gl[0] = make_float2(Store<S>::ld(g + n0), Store<S>::ld(g + n0 + 32));
+    gl[0] = make_float2(Store<GS(S)>::ld(g + n0), Store<GS(S)>::ld(g + n0 + 32));
 #pragma unroll
     for (int i = 1; i < 7; ++i) {
-        const SE<S> *q = g + opp7(i) * s + (int64_t)(n0 - G.off[i]);
-        gl[i] = make_float2(Store<S>::ld(q), Store<S>::ld(q + 32));
+        const SEG<S> *q = g + opp7(i) * s + (int64_t)(n0 - G.off[i]);
+        gl[i] = make_float2(Store<GS(S)>::ld(q), Store<GS(S)>::ld(q + 32));
     }
     const MacroT<float2> m = collide(P, fl, gl);
     f = opaque(f);
     g = opaque(g);
-    if (a0) Store<S>::st(f + n0, fl[0].x);
-    if (a1) Store<S>::st(f + n0 + 32, fl[0].y);
+    if (a0) Store<FS(S)>::st(f + n0, fl[0].x);
+    if (a1) Store<FS(S)>::st(f + n0 + 32, fl[0].y);
 #pragma unroll
     for (int i = 1; i < 19; ++i) {
-        SE<S> *q = f + i * s + (int64_t)(n0 + G.off[i]);
-        if (a0) Store<S>::st(q, fl[i].x);
-        if (a1) Store<S>::st(q + 32, fl[i].y);
+        SEF<S> *q = f + i * s + (int64_t)(n0 + G.off[i]);
+        if (a0) Store<FS(S)>::st(q, fl[i].x);
+        if (a1) Store<FS(S)>::st(q + 32, fl[i].y);
     }
-    if (a0) Store<S>::st(g + n0, gl[0].x);
-    if (a1) Store<S>::st(g + n0 + 32, gl[0].y);
+    if (a0) Store<GS(S)>::st(g + n0, gl[0].x);
+    if (a1) Store<GS(S)>::st(g + n0 + 32, gl[0].y);
 #pragma unroll
     for (int i = 1; i < 7; ++i) {
-        SE<S> *q = g + i * s + (int64_t)(n0 + G.off[i]);
-        if (a0) Store<S>::st(q, gl[i].x);
-        if (a1) Store<S>::st(q + 32, gl[i].y);
+        SEG<S> *q = g + i * s + (int64_t)(n0 + G.off[i]);
+        if (a0) Store<GS(S)>::st(q, gl[i].x);
+        if (a1) Store<GS(S)>::st(q + 32, gl[i].y);
     }
     if (MOM) {
         if (a0) {
@@ -366,7 +367,7 @@ __device__ __forceinline__ void k_aa_odd_rows_tile(SE<S> *__restrict__ f, SE<S> 
 }
 
 template <int S, bool MOM>
-__global__ void __launch_bounds__(256, 2) k_aa_odd_rows(SE<S> *__restrict__ f, SE<S> *__restrict__ g, Geom G,
+__global__ void __launch_bounds__(256, 2) k_aa_odd_rows(SEF<S> *__restrict__ f, SEG<S> *__restrict__ g, Geom G,
                                                         Phys P, float *__restrict__ mom) {
     k_aa_odd_rows_tile<S, MOM>(f, g, G, P, mom, blockIdx.x, threadIdx.x, blockDim.x);
 }
@@ -400,8 +401,8 @@ __global__ void __launch_bounds__(BS, BS == 128 ? 3 : 1)
                 sc = cells[st.cell];
             }
             __syncthreads();
-            SE<S> *f = static_cast<SE<S> *>(sc.f);
-            SE<S> *g = static_cast<SE<S> *>(sc.g);
+            SEF<S> *f = static_cast<SEF<S> *>(sc.f);
+            SEG<S> *g = static_cast<SEG<S> *>(sc.g);
             if (st.kind == TILE_EVEN)
                 k_aa_even2_tile<S, false>(f, g, sc.G, sc.P, nullptr, st.blk, threadIdx.x, BS);
             else if (st.kind == TILE_ROWS)
@@ -422,6 +423,7 @@ const void *batch_kernel_ptr(int storage, int block) {
     switch (storage) {
     case ST_F32: return batch_kernel<ST_F32>(block);
     case ST_F16: return batch_kernel<ST_F16>(block);
+    case ST_F16M: return batch_kernel<ST_F16M>(block);
     default: return batch_kernel<ST_BF16>(block);
     }
 }
@@ -444,8 +446,8 @@ cudaError_t launch_batch(int storage, const BatchArgs &a) {
 // ------------------------------------------------------ two-buffer pull ----
 
 template <int S, bool MOM>
-__global__ void __launch_bounds__(256, 3) k_pull(const SE<S> *__restrict__ fs, const SE<S> *__restrict__ gs,
-                                              SE<S> *__restrict__ fd, SE<S> *__restrict__ gd, Geom G,
+__global__ void __launch_bounds__(256, 3) k_pull(const SEF<S> *__restrict__ fs, const SEG<S> *__restrict__ gs,
+                                              SEF<S> *__restrict__ fd, SEG<S> *__restrict__ gd, Geom G,
                                               Phys P, float *__restrict__ mom) {
     const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= G.n) return;
@@ -459,9 +461,9 @@ __global__ void __launch_bounds__(256, 3) k_pull(const SE<S> *__restrict__ fs, c
     const Macro m = collide(P, fl, gl);
     const int64_t s = G.stride;
 #pragma unroll
-    for (int i = 0; i < 19; ++i) Store<S>::st(fd + i * s + n, fl[i]);
+    for (int i = 0; i < 19; ++i) Store<FS(S)>::st(fd + i * s + n, fl[i]);
 #pragma unroll
-    for (int i = 0; i < 7; ++i) Store<S>::st(gd + i * s + n, gl[i]);
+    for (int i = 0; i < 7; ++i) Store<GS(S)>::st(gd + i * s + n, gl[i]);
     if (MOM) write_sample(mom, s, n, m, neighbours(G, x, y, z), g0);
 }
 
@@ -472,14 +474,14 @@ __global__ void __launch_bounds__(256, 3) k_pull(const SE<S> *__restrict__ fs, c
 // B[j][m] = f_j(m + e_j), or, where m + e_j is behind a wall, the value that
 // bounces back into f_jbar(m).
 template <int S>
-__global__ void k_load(const float *__restrict__ st, SE<S> *__restrict__ f, SE<S> *__restrict__ g,
+__global__ void k_load(const float *__restrict__ st, SEF<S> *__restrict__ f, SEG<S> *__restrict__ g,
                        Geom G, Phys P, int layout) {
     const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= G.n) return;
     const int64_t s = G.stride, N = G.n;
     if (layout == LAYOUT_NATURAL) {
-        for (int i = 0; i < 19; ++i) Store<S>::st(f + i * s + n, st[i * N + n]);
-        for (int i = 0; i < 7; ++i) Store<S>::st(g + i * s + n, st[(19 + i) * N + n]);
+        for (int i = 0; i < 19; ++i) Store<FS(S)>::st(f + i * s + n, st[i * N + n]);
+        for (int i = 0; i < 7; ++i) Store<GS(S)>::st(g + i * s + n, st[(19 + i) * N + n]);
         return;
     }
     int x, y, z;
@@ -492,7 +494,7 @@ __global__ void k_load(const float *__restrict__ st, SE<S> *__restrict__ f, SE<S
             v = st[j * N + (int64_t)n + dst_off(b, ex19(j), ey19(j), ez19(j))];
         else
             v = st[opp19(j) * N + n];
-        Store<S>::st(f + j * s + n, v);
+        Store<FS(S)>::st(f + j * s + n, v);
     }
 #pragma unroll
     for (int j = 0; j < 7; ++j) {
@@ -504,13 +506,13 @@ __global__ void k_load(const float *__restrict__ st, SE<S> *__restrict__ f, SE<S
             const float gin = st[(19 + opp7(j)) * N + n];
             v = ((P.dir_mask >> fc) & 1) ? P.abbT[fc] - gin : gin;
         }
-        Store<S>::st(g + j * s + n, v);
+        Store<GS(S)>::st(g + j * s + n, v);
     }
 }
 
 // Device layout -> natural staging (float [26][n]).
 template <int S>
-__global__ void k_store(float *__restrict__ st, const SE<S> *__restrict__ f, const SE<S> *__restrict__ g,
+__global__ void k_store(float *__restrict__ st, const SEF<S> *__restrict__ f, const SEG<S> *__restrict__ g,
                         Geom G, Phys P, int layout) {
     const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= G.n) return;
@@ -528,7 +530,7 @@ __global__ void k_store(float *__restrict__ st, const SE<S> *__restrict__ f, con
 // Pre-collision populations of listed nodes -> out[k][26].
 template <int S>
 __global__ void k_gather(float *__restrict__ out, const int64_t *__restrict__ nodes, int64_t count,
-                         const SE<S> *__restrict__ f, const SE<S> *__restrict__ g, Geom G, Phys P,
+                         const SEF<S> *__restrict__ f, const SEG<S> *__restrict__ g, Geom G, Phys P,
                          int layout) {
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k >= count) return;
@@ -545,8 +547,8 @@ __global__ void k_gather(float *__restrict__ out, const int64_t *__restrict__ no
 
 // Diagnostic sample of the state -> mom[11][stride] (see write_sample).
 template <int S>
-__global__ void k_moments(float *__restrict__ mom, const SE<S> *__restrict__ f,
-                          const SE<S> *__restrict__ g, Geom G, Phys P, int layout) {
+__global__ void k_moments(float *__restrict__ mom, const SEF<S> *__restrict__ f,
+                          const SEG<S> *__restrict__ g, Geom G, Phys P, int layout) {
     const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= G.n) return;
     int x, y, z;
@@ -587,7 +589,8 @@ static inline unsigned blocks_for(int64_t n, int bs) { return (unsigned)((n + bs
 template <int S>
 static cudaError_t step_t(const StepArgs &a) {
     const unsigned nb = blocks_for(a.G.n, a.block);
-    auto f = static_cast<SE<S> *>(a.f), g = static_cast<SE<S> *>(a.g);
+    auto f = static_cast<SEF<S> *>(a.f);
+    auto g = static_cast<SEG<S> *>(a.g);
     if (a.scheme == 0 && a.wide) {
         if (a.parity == 0) {
             const unsigned nb2 = blocks_for((a.G.n + 1) / 2, a.block);
@@ -621,7 +624,8 @@ static cudaError_t step_t(const StepArgs &a) {
             }
         }
     } else {
-        auto f2 = static_cast<SE<S> *>(a.f2), g2 = static_cast<SE<S> *>(a.g2);
+        auto f2 = static_cast<SEF<S> *>(a.f2);
+        auto g2 = static_cast<SEG<S> *>(a.g2);
         if (a.mom) k_pull<S, true><<<nb, a.block, 0, a.stream>>>(f, g, f2, g2, a.G, a.P, a.mom);
         else k_pull<S, false><<<nb, a.block, 0, a.stream>>>(f, g, f2, g2, a.G, a.P, nullptr);
     }
@@ -632,6 +636,7 @@ cudaError_t launch_step(const StepArgs &a) {
     switch (a.storage) {
     case ST_F32: return step_t<ST_F32>(a);
     case ST_F16: return step_t<ST_F16>(a);
+    case ST_F16M: return step_t<ST_F16M>(a);
     default: return step_t<ST_BF16>(a);
     }
 }
@@ -640,9 +645,9 @@ template <int S>
 static cudaError_t convert_t(int op, float *st, void *f, void *g, const Geom &G, const Phys &P,
                              int layout, cudaStream_t stream) {
     const unsigned nb = blocks_for(G.n, 256);
-    if (op == 0) k_load<S><<<nb, 256, 0, stream>>>(st, (SE<S> *)f, (SE<S> *)g, G, P, layout);
-    else if (op == 1) k_store<S><<<nb, 256, 0, stream>>>(st, (const SE<S> *)f, (const SE<S> *)g, G, P, layout);
-    else k_moments<S><<<nb, 256, 0, stream>>>(st, (const SE<S> *)f, (const SE<S> *)g, G, P, layout);
+    if (op == 0) k_load<S><<<nb, 256, 0, stream>>>(st, (SEF<S> *)f, (SEG<S> *)g, G, P, layout);
+    else if (op == 1) k_store<S><<<nb, 256, 0, stream>>>(st, (const SEF<S> *)f, (const SEG<S> *)g, G, P, layout);
+    else k_moments<S><<<nb, 256, 0, stream>>>(st, (const SEF<S> *)f, (const SEG<S> *)g, G, P, layout);
     return cudaGetLastError();
 }
 
@@ -651,25 +656,27 @@ cudaError_t launch_convert(int storage, int op, float *st, void *f, void *g, con
     switch (storage) {
     case ST_F32: return convert_t<ST_F32>(op, st, f, g, G, P, layout, stream);
     case ST_F16: return convert_t<ST_F16>(op, st, f, g, G, P, layout, stream);
+    case ST_F16M: return convert_t<ST_F16M>(op, st, f, g, G, P, layout, stream);
     default: return convert_t<ST_BF16>(op, st, f, g, G, P, layout, stream);
     }
 }
 
+template <int S>
+static cudaError_t gather_t(float *out, const int64_t *nodes, int64_t count, const void *f, const void *g,
+                            const Geom &G, const Phys &P, int layout, cudaStream_t stream) {
+    k_gather<S><<<blocks_for(count, 128), 128, 0, stream>>>(out, nodes, count, (const SEF<S> *)f,
+                                                             (const SEG<S> *)g, G, P, layout);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_gather(int storage, float *out, const int64_t *nodes, int64_t count, const void *f,
                           const void *g, const Geom &G, const Phys &P, int layout, cudaStream_t stream) {
-    const unsigned nb = blocks_for(count, 128);
     switch (storage) {
-    case ST_F32:
-        k_gather<ST_F32><<<nb, 128, 0, stream>>>(out, nodes, count, (const float *)f, (const float *)g, G, P, layout);
-        break;
-    case ST_F16:
-        k_gather<ST_F16><<<nb, 128, 0, stream>>>(out, nodes, count, (const __half *)f, (const __half *)g, G, P, layout);
-        break;
-    default:
-        k_gather<ST_BF16><<<nb, 128, 0, stream>>>(out, nodes, count, (const __nv_bfloat16 *)f,
-                                                  (const __nv_bfloat16 *)g, G, P, layout);
+    case ST_F32: return gather_t<ST_F32>(out, nodes, count, f, g, G, P, layout, stream);
+    case ST_F16: return gather_t<ST_F16>(out, nodes, count, f, g, G, P, layout, stream);
+    case ST_F16M: return gather_t<ST_F16M>(out, nodes, count, f, g, G, P, layout, stream);
+    default: return gather_t<ST_BF16>(out, nodes, count, f, g, G, P, layout, stream);
     }
-    return cudaGetLastError();
 }
 
 cudaError_t launch_equilibrium(float *st, const float *fields, uint32_t n, const Phys &P,

@@ -236,9 +236,11 @@ __global__ void k_up_bwd(const float *__restrict__ dy, int C, int D, int H, int 
     }
 }
 
+// Source index pair and weight of output node j (coordinate in FP64: in FP32
+// the rounding of (j + 1/2) n_in / n_out near n_in = 64 reaches 4e-6).
 __device__ __forceinline__ void lin_idx(int j, int n_out, int n_in, int &i0, int &i1, float &f) {
-    float s = ((float)j + 0.5f) * (float)n_in / (float)n_out - 0.5f;
-    if (s <= 0.f) {
+    const double s = ((double)j + 0.5) * (double)n_in / (double)n_out - 0.5;
+    if (s <= 0.0) {
         i0 = i1 = 0;
         f = 0.f;
         return;
@@ -250,7 +252,7 @@ __device__ __forceinline__ void lin_idx(int j, int n_out, int n_in, int &i0, int
         return;
     }
     i1 = i0 + 1;
-    f = s - (float)i0;
+    f = (float)(s - (double)i0);
 }
 
 __global__ void k_trilinear(const float *__restrict__ x, int C, int d, int h, int w, float *__restrict__ y, int D,

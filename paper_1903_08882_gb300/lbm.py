@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_PKG, "liblbm_gb300.so")
 
 LBM_OK, LBM_ERR_PARAM, LBM_ERR_CUDA, LBM_ERR_OOM, LBM_ERR_DIVERGED, LBM_ERR_TIMEOUT, LBM_ERR_STATE = range(7)
 ADIABATIC, DIRICHLET, PERIODIC = 0, 1, 2
-STORAGE = {"fp32": 0, "fp16s": 1, "bf16s": 2}
+STORAGE = {"fp32": 0, "fp16s": 1, "bf16s": 2, "fp16m": 3}
 STREAMING = {"aa": 0, "pull2": 1}
 NDIAG = 24
 

@@ -44,7 +44,8 @@ def main():
         samples += 1
         if k % 10 == 0:
             d = oracle.finalize(p, r)
-            series.append([k * every, d["Nu_vol"], 0.5 * (d["Nu_face"][4] - d["Nu_face"][5]), d["Re_rms"]])
+            series.append([k * every, d["Nu_vol"], 0.5 * (d["Nu_face"][4] - d["Nu_face"][5]), d["Re_rms"],
+                           d["Nu_kin"], d["Nu_th"], d["Re_w"]])
             sys.stderr.write(f"sample {k} Nu_vol {d['Nu_vol']:.4f} Re {d['Re_rms']:.3f}\n")
             sys.stderr.flush()
         f, g = oracle.run(p, f, g, every)
@@ -56,7 +57,7 @@ def main():
         "Re_rms": float(d["Re_rms"]), "Re_w": float(d["Re_w"]), "Nu_vol": float(d["Nu_vol"]),
         "Nu_wall": float(0.5 * (d["Nu_face"][4] - d["Nu_face"][5])), "Nu_kin": float(d["Nu_kin"]),
         "Nu_th": float(d["Nu_th"]), "E": float(d["E"]),
-        "series_step_Nuvol_Nuwall_Re": series, "cpu_seconds": round(time.time() - t0, 1),
+        "series_step_Nuvol_Nuwall_Re": series,  # rows: step, Nu_vol, Nu_wall, Re_rms[, Nu_kin, Nu_th, Re_w] "cpu_seconds": round(time.time() - t0, 1),
     }
     print(json.dumps(out, indent=1))
 

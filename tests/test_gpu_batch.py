@@ -44,7 +44,7 @@ def _make(lbm, storage="fp32"):
     return lats
 
 
-@pytest.mark.parametrize("storage", ["fp32", "fp16s"])
+@pytest.mark.parametrize("storage", ["fp32", "fp16s", "fp16m"])
 def test_batch_matches_single_cells(lbm, storage):
     import torch
 

