@@ -57,7 +57,9 @@ def main():
         "Re_rms": float(d["Re_rms"]), "Re_w": float(d["Re_w"]), "Nu_vol": float(d["Nu_vol"]),
         "Nu_wall": float(0.5 * (d["Nu_face"][4] - d["Nu_face"][5])), "Nu_kin": float(d["Nu_kin"]),
         "Nu_th": float(d["Nu_th"]), "E": float(d["E"]),
-        "series_step_Nuvol_Nuwall_Re": series,  # rows: step, Nu_vol, Nu_wall, Re_rms[, Nu_kin, Nu_th, Re_w] "cpu_seconds": round(time.time() - t0, 1),
+        # rows: step, Nu_vol, Nu_wall, Re_rms, Nu_kin, Nu_th, Re_w
+        "series_step_Nuvol_Nuwall_Re": series,
+        "cpu_seconds": round(time.time() - t0, 1),
     }
     print(json.dumps(out, indent=1))
 
