@@ -4,12 +4,12 @@ Plain PyTorch CPU ops in float64; gradients come from autograd.  Only tests
 import this module.  It shares no code with the CUDA path; the architecture
 below is written out from its description:
 
-  input 6 channels (log10 Ra, Pr, and the coarse u, v, w, T trilinearly
-  upsampled); 4 levels with 16, 32, 48, 64 channels; two 3x3x3 convolutions
+  input 7 channels (log10 Ra, Pr, and the coarse u, v, w, T and density
+  deviation trilinearly upsampled); 4 levels with 16, 32, 48, 64 channels; two 3x3x3 convolutions
   with ReLU per level; average pooling by 2 (ceil sizes) down, nearest
   upsampling by 2 (cropped to the skip's size) up; skip connections
-  concatenated after the upsampled channels; a 3x3x3 head to 4 channels added
-  to the upsampled coarse (u, v, w, T).
+  concatenated after the upsampled channels; a 3x3x3 head to 5 channels added
+  to the upsampled coarse (u, v, w, T, density deviation).
 
 Weights are FP64 copies of the BF16-rounded weights the GPU uses; the tap
 order of a weight row [Cout][Cin][27] is dz, dy, dx in -1, 0, 1 with dx
@@ -22,7 +22,7 @@ import torch
 import torch.nn.functional as F
 
 CH = (16, 32, 48, 64)
-IN_CH, OUT_CH = 6, 4
+IN_CH, OUT_CH = 7, 5
 
 
 def layer_shapes():
@@ -65,7 +65,7 @@ def up(x, size):
 
 
 def forward(params, x):
-    """params: dict name -> (w [Cout][Cin][27], b [Cout]) float64; x [6][D][H][W]."""
+    """params: dict name -> (w [Cout][Cin][27], b [Cout]) float64; x [7][D][H][W]."""
     def block(name, t):
         w, b = params[name]
         return F.relu(conv(t, w, b))
@@ -82,7 +82,7 @@ def forward(params, x):
         t = torch.cat([up(t, s.shape[1:]), s], dim=0)
         t = block(f"d{l}b", block(f"d{l}a", t))
     w, b = params["head"]
-    return conv(t, w, b) + x[2:6]
+    return conv(t, w, b) + x[2:7]
 
 
 def loss_and_grads(params, x, target):

@@ -73,3 +73,14 @@ def cell_candidates(seed: int, count: int, edges=(33, 49, 65, 81, 97)):
         edge = edges[min(int(e[i] * len(edges)), len(edges) - 1)]
         out.append((edge, float(10.0 ** (4.0 + 3.0 * r[i])), 0.71 if p[i] < 0.5 else 7.0))
     return out
+
+
+def warmstart_pairs(seed: int, count: int, ra_range=(1e5, 1e7), pr_range=(0.5, 7.0), stream: int = 41):
+    """Seeded (Ra, Pr) draws for the learned warm start: Ra log-uniform and Pr
+    uniform over the given ranges."""
+    k = np.arange(count, dtype=np.uint64)
+    r = uniform(seed, stream, k)
+    p = uniform(seed, stream + 1, k)
+    lo, hi = np.log10(ra_range[0]), np.log10(ra_range[1])
+    return [(float(10.0 ** (lo + (hi - lo) * r[i])), float(pr_range[0] + (pr_range[1] - pr_range[0]) * p[i]))
+            for i in range(count)]

@@ -1,13 +1,13 @@
 """The warm-start network on the GPU: a 3D U-Net driven through the kernels of
 include/lbm_nn.h.
 
-Architecture: input 6 channels (log10 Ra, Pr and the coarse steady u, v, w, T
-trilinearly upsampled to the fine lattice); four levels with 16, 32, 48 and
+Architecture: input 7 channels (log10 Ra, Pr and the coarse steady u, v, w, T
+and density deviation, trilinearly upsampled to the fine lattice); four levels with 16, 32, 48 and
 64 channels, each two 3x3x3 convolutions with ReLU; average pooling by 2
 (ceil sizes) on the way down and nearest upsampling by 2 on the way up, the
 skip of each level concatenated after the upsampled channels; a 3x3x3 head
-to 4 channels added to the upsampled coarse (u, v, w, T), so the network
-learns the fine-minus-coarse correction.  BF16 weights, FP32 accumulation,
+to 5 channels added to the upsampled coarse (u, v, w, T, density deviation),
+so the network learns the fine-minus-coarse correction.  BF16 weights, FP32 accumulation,
 FP32 master weights for Adam.
 
 This module only allocates buffers (PyTorch tensors: device memory) and
@@ -22,7 +22,7 @@ import numpy as np
 from . import lbm as _lbm
 
 CH = (16, 32, 48, 64)
-IN_CH, OUT_CH = 6, 4
+IN_CH, OUT_CH = 7, 5
 
 _fp, _u16p, _dp = ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p
 
@@ -205,7 +205,7 @@ class UNet:
         return t[CH[l + 1]:]
 
     def forward(self, x):
-        """x: [6][D][H][W] float32 on the GPU; returns the output buffer."""
+        """x: [7][D][H][W] float32 on the GPU; returns the output buffer."""
         b, P = self.buf, self.params
         t = x
         for l in range(4):
@@ -226,7 +226,7 @@ class UNet:
             t = b[f"d{l}"]
         ph = P["head"]
         conv_forward(t, ph["wb"], ph["b"], OUT_CH, b["out"], False)
-        axpy(1.0, x[2:6].contiguous() if not x[2:6].is_contiguous() else x[2:6], b["out"])
+        axpy(1.0, x[2:7].contiguous() if not x[2:7].is_contiguous() else x[2:7], b["out"])
         return b["out"]
 
     def _conv_back(self, name, x, y, gy, gx, relu=True, accumulate=False):

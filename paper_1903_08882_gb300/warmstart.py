@@ -1,0 +1,212 @@
+"""Learned warm start of the steady side-heated cell.
+
+Pipeline (all lattice work in the CUDA library, all network work in the
+kernels of include/lbm_nn.h; this module sequences them):
+  1. steady fields of the side-heated cell for seeded (Ra, Pr) draws, on a
+     coarse (33^3) and a fine (65^3) lattice, solved by the lattice Boltzmann
+     library itself (batched cells, steady criterion on the hot-wall Nu);
+  2. the 3D U-Net (unet.py) trained on them with Adam: input log10(Ra), Pr and
+     the coarse (u/U, v/U, w/U, T, (rho - 1)/U^2) trilinearly upsampled; target
+     the fine ones.  The density deviation is part of the prediction because a
+     start with the wrong density excites acoustic modes that the bulk
+     viscosity damps only over ~1e5 steps;
+  3. evaluation on held-out draws: steps to the steady state from rest
+     against steps from the network's prediction, at the same criterion.  A
+     prediction whose hot-wall Nu still moves by more than `fallback_tol`
+     (relative) over its first 1000 steps is judged too far off, and the run
+     restarts from rest (cold start fallback).
+
+  python -m paper_1903_08882_gb300.warmstart --train 400 --test 32 --out report.json
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+
+from . import drivers, inputs
+from . import lbm as L
+
+COARSE, FINE = 33, 65
+U = 0.1
+
+
+def _norm_inputs(Ra, Pr):
+    return (np.log10(Ra) - 6.0), (Pr - 3.75) / 3.25
+
+
+def steady_set(pairs, N, stream, group=32, every=1000, tol=1e-7, max_steps=300_000, storage="fp32"):
+    """Steady fields (5, N, N, N) float32 [u/U, v/U, w/U, T, (rho-1)/U^2] for each (Ra, Pr),
+    solved in batched groups.  Returns (fields, steps, converged, Nu_hot); a
+    cell that diverges gets fields None."""
+    out_f, out_s, out_c, out_nu = [], [], [], []
+    for g0 in range(0, len(pairs), group):
+        chunk = pairs[g0:g0 + group]
+        lats = [L.Lattice(N, N, N, L.walls_side_heated(), Ra=Ra, Pr=Pr, U=U, storage=storage, stream=stream)
+                for Ra, Pr in chunk]
+        prev = [None] * len(lats)
+        done = [None] * len(lats)
+        steps = 0
+        with L.Batch(lats, stream=stream) as b:
+            b.set_schedule(block_size=128, blocks_per_sm=3, steps_per_launch=100, graph_chunk=every)
+            while steps < max_steps and any(d is None for d in done):
+                b.step(every)
+                steps += every
+                for k, lat in enumerate(lats):
+                    if done[k] is not None:
+                        continue
+                    lat.sample()
+                    d = lat.diagnostics(reset=True, raise_on_diverged=False)
+                    nu = d["Nu_face"][0]
+                    if d["diverged"] or not np.isfinite(nu):
+                        done[k] = ("diverged", steps, np.nan)
+                    elif prev[k] is not None and abs(nu - prev[k]) <= tol * abs(nu):
+                        done[k] = ("converged", steps, nu)
+                    prev[k] = nu
+        for k, lat in enumerate(lats):
+            state = done[k] if done[k] is not None else ("max_steps", steps, prev[k])
+            if state[0] == "diverged":
+                out_f.append(None)
+            else:
+                rho, u3, T = lat.moments()
+                out_f.append(np.concatenate([u3 / U, T[None], (rho[None] - 1.0) / U**2]).astype(np.float32))
+            out_s.append(state[1])
+            out_c.append(state[0] == "converged")
+            out_nu.append(state[2])
+            lat.close()
+    return out_f, out_s, out_c, out_nu
+
+
+class Trainer:
+    def __init__(self, seed=0):
+        import torch
+
+        from .unet import UNet
+
+        self.torch = torch
+        self.net = UNet((FINE, FINE, FINE), seed=seed)
+
+    def make_input(self, coarse, Ra, Pr):
+        torch = self.torch
+        from .unet import trilinear
+
+        x = torch.empty((7, FINE, FINE, FINE), device="cuda")
+        a, b = _norm_inputs(Ra, Pr)
+        x[0].fill_(a)
+        x[1].fill_(b)
+        trilinear(torch.from_numpy(coarse).cuda(), x[2:7])
+        return x
+
+    def fit(self, xs, ys, epochs=30, lr=2e-3, batch=8, seed=0, log=None):
+        rng = np.random.default_rng(seed)
+        net = self.net
+        hist = []
+        for ep in range(epochs):
+            order = rng.permutation(len(xs))
+            tot = 0.0
+            for k0 in range(0, len(order), batch):
+                net.zero_grad()
+                for k in order[k0:k0 + batch]:
+                    net.forward(xs[k])
+                    tot += net.backward(xs[k], ys[k]).item()
+                # the accumulated gradient is a sum over the batch
+                net.adam_step(lr / batch)
+            hist.append(tot / len(xs))
+            if log:
+                log(f"epoch {ep} loss {hist[-1]:.3e}")
+        return hist
+
+    def predict(self, x):
+        out = self.net.forward(x)
+        return out.detach().cpu().numpy()
+
+
+def run_from(Ra, Pr, fields, stream, tol=1e-7, fallback_tol=None, max_steps=400_000):
+    """Steps to the steady state from `fields` (None: from rest)."""
+    with L.Lattice(FINE, FINE, FINE, L.walls_side_heated(), Ra=Ra, Pr=Pr, U=U, stream=stream) as lat:
+        fell_back = False
+        if fields is not None:
+            rho = 1.0 + fields[4].astype(np.float64) * U**2
+            lat.set_fields(rho, fields[:3].astype(np.float64) * U, fields[3].astype(np.float64))
+            if fallback_tol is not None:
+                lat.sample()
+                nu0 = lat.diagnostics()["Nu_face"][0]
+                lat.step(1000)
+                lat.sample()
+                nu1 = lat.diagnostics()["Nu_face"][0]
+                if not np.isfinite(nu1) or abs(nu1 - nu0) > fallback_tol * abs(nu1):
+                    fell_back = True
+                    lat.set_fields(1.0, np.zeros(3), 0.0)
+        r = drivers.run_to_steady(lat, every=1000, tol=tol, max_steps=max_steps)
+        extra = 1000 if (fields is not None and fallback_tol is not None) else 0
+        return dict(steps=r["steps"] + extra, converged=r["converged"], Nu=float(r["Nu"]), fell_back=fell_back)
+
+
+def main():
+    import torch
+
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--train", type=int, default=400)
+    ap.add_argument("--test", type=int, default=32)
+    ap.add_argument("--epochs", type=int, default=30)
+    ap.add_argument("--seed", type=int, default=190308882)
+    ap.add_argument("--out", default="warmstart_report.json")
+    ap.add_argument("--weights", default=None, help="save the trained BF16 weights (npz)")
+    args = ap.parse_args()
+    t0 = time.time()
+    log = lambda m: print(f"[{time.time() - t0:7.1f}s] {m}", flush=True)  # noqa: E731
+    stream = torch.cuda.Stream()
+    report = {"coarse": COARSE, "fine": FINE, "U": U}
+    with torch.cuda.stream(stream):
+        pairs = inputs.warmstart_pairs(args.seed, args.train + args.test + 64)
+        # the held-out set ends with the case the FP64 oracle has a steady state for
+        test_pairs = pairs[args.train:args.train + args.test - 1] + [(1e6, 0.71)]
+        train_pairs = pairs[:args.train]
+        log(f"coarse solves: {len(train_pairs) + len(test_pairs)}")
+        cf, cs, cc, _ = steady_set(train_pairs + test_pairs, COARSE, stream)
+        log(f"coarse done: converged {sum(cc)}, diverged {sum(f is None for f in cf)}")
+        tr = [i for i in range(len(train_pairs)) if cf[i] is not None]
+        ff, fs, fc, fnu = steady_set([train_pairs[i] for i in tr], FINE, stream)
+        log(f"fine training solves done: converged {sum(fc)}, mean steps {np.mean(fs):.0f}")
+        keep = [j for j in range(len(tr)) if ff[j] is not None]
+        trainer = Trainer(seed=1)
+        xs = [trainer.make_input(cf[tr[j]], *train_pairs[tr[j]]) for j in keep]
+        ys = [torch.from_numpy(ff[j]).cuda() for j in keep]
+        report["train_samples"] = len(xs)
+        hist = trainer.fit(xs, ys, epochs=args.epochs, log=log)
+        report["loss_history"] = hist
+        del xs, ys
+        results = []
+        for k, (Ra, Pr) in enumerate(test_pairs):
+            c = cf[len(train_pairs) + k]
+            if c is None:
+                results.append(dict(Ra=Ra, Pr=Pr, skipped="coarse solve diverged"))
+                continue
+            x = trainer.make_input(c, Ra, Pr)
+            pred = trainer.predict(x)
+            cold = run_from(Ra, Pr, None, stream)
+            warm = run_from(Ra, Pr, pred, stream, fallback_tol=5e-2)
+            up = x[2:7].detach().cpu().numpy()
+            interp = run_from(Ra, Pr, up, stream)
+            results.append(dict(Ra=Ra, Pr=Pr, cold=cold, warm=warm, upsampled_coarse=interp,
+                                speedup=cold["steps"] / max(warm["steps"], 1)))
+            log(f"test {k}: Ra {Ra:.3g} Pr {Pr:.2f} cold {cold['steps']} warm {warm['steps']} "
+                f"coarse-only {interp['steps']} Nu {cold['Nu']:.5f}/{warm['Nu']:.5f}")
+        report["tests"] = results
+        sp = [r["speedup"] for r in results if "speedup" in r]
+        report["median_speedup"] = float(np.median(sp)) if sp else None
+        report["mean_steps_cold"] = float(np.mean([r["cold"]["steps"] for r in results if "cold" in r]))
+        report["mean_steps_warm"] = float(np.mean([r["warm"]["steps"] for r in results if "warm" in r]))
+        report["wall_seconds"] = round(time.time() - t0, 1)
+        if args.weights:
+            np.savez_compressed(args.weights, **{k: p["wb"].cpu().numpy() for k, p in trainer.net.params.items()},
+                                **{k + "_b": p["b"].cpu().numpy() for k, p in trainer.net.params.items()})
+    with open(args.out, "w") as fh:
+        json.dump(report, fh, indent=1)
+    log(f"median speedup {report['median_speedup']}")
+
+
+if __name__ == "__main__":
+    main()

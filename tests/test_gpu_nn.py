@@ -116,8 +116,8 @@ def test_network_output_and_gradients(U):
     size = (17, 17, 17)
     net = U.UNet(size, seed=3)
     g = torch.Generator().manual_seed(5)
-    x = torch.rand((6,) + size, generator=g, dtype=torch.float64) - 0.5
-    t = torch.rand((4,) + size, generator=g, dtype=torch.float64) - 0.5
+    x = torch.rand((7,) + size, generator=g, dtype=torch.float64) - 0.5
+    t = torch.rand((5,) + size, generator=g, dtype=torch.float64) - 0.5
     out = net.forward(x.float().cuda())
     net.zero_grad()
     loss = net.backward(x.float().cuda(), t.float().cuda())
@@ -134,8 +134,8 @@ def test_training_reduces_loss(U):
     size = (17, 17, 17)
     net = U.UNet(size, seed=4)
     g = torch.Generator().manual_seed(6)
-    x = (torch.rand((6,) + size, generator=g) - 0.5).cuda()
-    t = 0.5 * x[2:6].clone()  # a learnable target: halve the residual input
+    x = (torch.rand((7,) + size, generator=g) - 0.5).cuda()
+    t = 0.5 * x[2:7].clone()  # a learnable target: halve the residual input
     losses = []
     for _ in range(60):
         net.zero_grad()

@@ -57,8 +57,8 @@ def _params(seed, scale=0.3):
 def test_gradient_against_finite_differences():
     g = torch.Generator().manual_seed(3)
     size = (7, 6, 5)
-    x = torch.rand((6,) + size, generator=g, dtype=torch.float64) - 0.5
-    t = torch.rand((4,) + size, generator=g, dtype=torch.float64) - 0.5
+    x = torch.rand((7,) + size, generator=g, dtype=torch.float64) - 0.5
+    t = torch.rand((5,) + size, generator=g, dtype=torch.float64) - 0.5
     P = _params(4)
     _, loss, grads = R.loss_and_grads(P, x, t)
     # directional derivative along a random direction of all parameters
