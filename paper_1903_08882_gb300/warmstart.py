@@ -14,7 +14,8 @@ kernels of include/lbm_nn.h; this module sequences them):
      against steps from the network's prediction, at the same criterion.  A
      prediction whose hot-wall Nu still moves by more than `fallback_tol`
      (relative) over its first 1000 steps is judged too far off, and the run
-     restarts from rest (cold start fallback).
+     restarts from rest (cold start fallback).  Training fields are solved from
+the upsampled coarse solution, which reaches the same steady state sooner.
 
   python -m paper_1903_08882_gb300.warmstart --train 400 --test 32 --out report.json
 """
@@ -31,21 +32,31 @@ from . import lbm as L
 
 COARSE, FINE = 33, 65
 U = 0.1
+# a warm start whose hot-wall Nu moves by more than this (relative) over its
+# first 1000 steps is judged a failed prediction and restarted from rest
+FALLBACK_TOL = 0.2
 
 
 def _norm_inputs(Ra, Pr):
     return (np.log10(Ra) - 6.0), (Pr - 3.75) / 3.25
 
 
-def steady_set(pairs, N, stream, group=32, every=1000, tol=1e-7, max_steps=300_000, storage="fp32"):
+def steady_set(pairs, N, stream, group=32, every=1000, tol=1e-7, max_steps=300_000, storage="fp32", starts=None):
     """Steady fields (5, N, N, N) float32 [u/U, v/U, w/U, T, (rho-1)/U^2] for each (Ra, Pr),
-    solved in batched groups.  Returns (fields, steps, converged, Nu_hot); a
-    cell that diverges gets fields None."""
+    solved in batched groups, from rest or from the given start fields (the
+    steady state does not depend on the start).  Returns (fields, steps,
+    converged, Nu_hot); a cell that diverges gets fields None."""
     out_f, out_s, out_c, out_nu = [], [], [], []
     for g0 in range(0, len(pairs), group):
         chunk = pairs[g0:g0 + group]
         lats = [L.Lattice(N, N, N, L.walls_side_heated(), Ra=Ra, Pr=Pr, U=U, storage=storage, stream=stream)
                 for Ra, Pr in chunk]
+        if starts is not None:
+            for k, lat in enumerate(lats):
+                s0 = starts[g0 + k]
+                if s0 is not None:
+                    lat.set_fields(1.0 + s0[4].astype(np.float64) * U**2, s0[:3].astype(np.float64) * U,
+                                   s0[3].astype(np.float64))
         prev = [None] * len(lats)
         done = [None] * len(lats)
         steps = 0
@@ -79,6 +90,17 @@ def steady_set(pairs, N, stream, group=32, every=1000, tol=1e-7, max_steps=300_0
     return out_f, out_s, out_c, out_nu
 
 
+def upsample(coarse):
+    """Coarse fields (5, n, n, n) -> (5, FINE, FINE, FINE) on the GPU (trilinear kernel)."""
+    import torch
+
+    from .unet import trilinear
+
+    y = torch.empty((5, FINE, FINE, FINE), device="cuda")
+    trilinear(torch.from_numpy(coarse).cuda(), y)
+    return y
+
+
 class Trainer:
     def __init__(self, seed=0):
         import torch
@@ -88,22 +110,38 @@ class Trainer:
         self.torch = torch
         self.net = UNet((FINE, FINE, FINE), seed=seed)
 
+    # per-channel scale of the five field channels (inputs and targets alike):
+    # the inverse standard deviation of each fine field over the training set
+    scale = np.ones(5, dtype=np.float32)
+
+    def upsample(self, coarse):
+        return upsample(coarse)
+
     def make_input(self, coarse, Ra, Pr):
         torch = self.torch
-        from .unet import trilinear
-
         x = torch.empty((7, FINE, FINE, FINE), device="cuda")
         a, b = _norm_inputs(Ra, Pr)
         x[0].fill_(a)
         x[1].fill_(b)
-        trilinear(torch.from_numpy(coarse).cuda(), x[2:7])
+        x[2:7] = self.upsample(coarse) * torch.from_numpy(self.scale).cuda().view(5, 1, 1, 1)
         return x
 
-    def fit(self, xs, ys, epochs=30, lr=2e-3, batch=8, seed=0, log=None):
+    def set_scale(self, fine_list):
+        acc = np.zeros(5)
+        for f in fine_list:
+            acc += (f.astype(np.float64) ** 2).mean(axis=(1, 2, 3))
+        self.scale = (1.0 / np.sqrt(acc / len(fine_list) + 1e-30)).astype(np.float32)
+
+    def target(self, fine):
+        return self.torch.from_numpy(fine * self.scale.reshape(5, 1, 1, 1)).cuda()
+
+    def fit(self, xs, ys, epochs=60, lr=2e-3, lr_min=2e-5, batch=8, seed=0, log=None):
+        """Adam with a cosine learning-rate decay from lr to lr_min."""
         rng = np.random.default_rng(seed)
         net = self.net
         hist = []
         for ep in range(epochs):
+            lr_ep = lr_min + 0.5 * (lr - lr_min) * (1 + np.cos(np.pi * ep / max(epochs - 1, 1)))
             order = rng.permutation(len(xs))
             tot = 0.0
             for k0 in range(0, len(order), batch):
@@ -112,7 +150,7 @@ class Trainer:
                     net.forward(xs[k])
                     tot += net.backward(xs[k], ys[k]).item()
                 # the accumulated gradient is a sum over the batch
-                net.adam_step(lr / batch)
+                net.adam_step(lr_ep / batch)
             hist.append(tot / len(xs))
             if log:
                 log(f"epoch {ep} loss {hist[-1]:.3e}")
@@ -120,7 +158,20 @@ class Trainer:
 
     def predict(self, x):
         out = self.net.forward(x)
-        return out.detach().cpu().numpy()
+        return out.detach().cpu().numpy() / self.scale.reshape(5, 1, 1, 1)
+
+    def save(self, path):
+        np.savez_compressed(path, scale=self.scale,
+                            **{k: p["wb"].cpu().numpy() for k, p in self.net.params.items()},
+                            **{k + "_b": p["b"].cpu().numpy() for k, p in self.net.params.items()})
+
+    def load(self, path):
+        torch = self.torch
+        z = np.load(path)
+        self.scale = z["scale"].astype(np.float32)
+        for k, p in self.net.params.items():
+            p["wb"].copy_(torch.from_numpy(z[k]))
+            p["b"].copy_(torch.from_numpy(z[k + "_b"]))
 
 
 def run_from(Ra, Pr, fields, stream, tol=1e-7, fallback_tol=None, max_steps=400_000):
@@ -150,7 +201,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--train", type=int, default=400)
     ap.add_argument("--test", type=int, default=32)
-    ap.add_argument("--epochs", type=int, default=30)
+    ap.add_argument("--epochs", type=int, default=60)
     ap.add_argument("--seed", type=int, default=190308882)
     ap.add_argument("--out", default="warmstart_report.json")
     ap.add_argument("--weights", default=None, help="save the trained BF16 weights (npz)")
@@ -168,12 +219,16 @@ def main():
         cf, cs, cc, _ = steady_set(train_pairs + test_pairs, COARSE, stream)
         log(f"coarse done: converged {sum(cc)}, diverged {sum(f is None for f in cf)}")
         tr = [i for i in range(len(train_pairs)) if cf[i] is not None]
-        ff, fs, fc, fnu = steady_set([train_pairs[i] for i in tr], FINE, stream)
+        starts = [upsample(cf[i]).cpu().numpy() for i in tr]
+        ff, fs, fc, fnu = steady_set([train_pairs[i] for i in tr], FINE, stream, starts=starts)
+        del starts
         log(f"fine training solves done: converged {sum(fc)}, mean steps {np.mean(fs):.0f}")
         keep = [j for j in range(len(tr)) if ff[j] is not None]
         trainer = Trainer(seed=1)
+        trainer.set_scale([ff[j] for j in keep])
+        report["channel_scale"] = trainer.scale.tolist()
         xs = [trainer.make_input(cf[tr[j]], *train_pairs[tr[j]]) for j in keep]
-        ys = [torch.from_numpy(ff[j]).cuda() for j in keep]
+        ys = [trainer.target(ff[j]) for j in keep]
         report["train_samples"] = len(xs)
         hist = trainer.fit(xs, ys, epochs=args.epochs, log=log)
         report["loss_history"] = hist
@@ -187,8 +242,8 @@ def main():
             x = trainer.make_input(c, Ra, Pr)
             pred = trainer.predict(x)
             cold = run_from(Ra, Pr, None, stream)
-            warm = run_from(Ra, Pr, pred, stream, fallback_tol=5e-2)
-            up = x[2:7].detach().cpu().numpy()
+            warm = run_from(Ra, Pr, pred, stream, fallback_tol=FALLBACK_TOL)
+            up = trainer.upsample(c).cpu().numpy()
             interp = run_from(Ra, Pr, up, stream)
             results.append(dict(Ra=Ra, Pr=Pr, cold=cold, warm=warm, upsampled_coarse=interp,
                                 speedup=cold["steps"] / max(warm["steps"], 1)))
@@ -201,8 +256,7 @@ def main():
         report["mean_steps_warm"] = float(np.mean([r["warm"]["steps"] for r in results if "warm" in r]))
         report["wall_seconds"] = round(time.time() - t0, 1)
         if args.weights:
-            np.savez_compressed(args.weights, **{k: p["wb"].cpu().numpy() for k, p in trainer.net.params.items()},
-                                **{k + "_b": p["b"].cpu().numpy() for k, p in trainer.net.params.items()})
+            trainer.save(args.weights)
     with open(args.out, "w") as fh:
         json.dump(report, fh, indent=1)
     log(f"median speedup {report['median_speedup']}")

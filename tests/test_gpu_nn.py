@@ -135,11 +135,13 @@ def test_training_reduces_loss(U):
     net = U.UNet(size, seed=4)
     g = torch.Generator().manual_seed(6)
     x = (torch.rand((7,) + size, generator=g) - 0.5).cuda()
-    t = 0.5 * x[2:7].clone()  # a learnable target: halve the residual input
+    # a target the network can reach: the residual input shifted per channel
+    shift = torch.tensor([0.1, -0.05, 0.08, 0.02, -0.1], device="cuda").view(5, 1, 1, 1)
+    t = x[2:7] + shift
     losses = []
-    for _ in range(60):
+    for _ in range(40):
         net.zero_grad()
         net.forward(x)
         losses.append(net.backward(x, t).item())
-        net.adam_step(1e-2)
-    assert losses[-1] < 0.6 * losses[0], losses[::10]
+        net.adam_step(3e-3)
+    assert losses[-1] < 0.3 * losses[0], losses[::8]
