@@ -93,6 +93,11 @@ typedef struct {
     int diag_every; /* lbm_step samples the diagnostics every diag_every steps (0: never) */
     int block_size; /* threads per block of the step kernels, 0 = library default */
     int nodes_per_thread; /* AA step kernels: 1, or 2 (packed FP32 arithmetic); 0 = library default (2) */
+    int pipeline; /* AA steps without a diagnostic sample: 1 = register kernels (each thread loads its
+                     populations into registers), 2 = staged kernels (persistent blocks copy the
+                     population windows of the next tiles into shared memory with bulk asynchronous
+                     copies while the current tile is updated; LBM_ERR_PARAM where they cannot run),
+                     0 = library default (register for LBM_FP32, staged for the others) */
 } lbm_params;
 
 /* Device memory provider.  alloc returns device memory of at least `bytes`
@@ -205,8 +210,17 @@ lbm_status lbm_sample(lbm_ctx *ctx);
  * filled) when the last sample saw a non-finite moment or max |u| > 1/sqrt(3). */
 lbm_status lbm_diagnostics(lbm_ctx *ctx, lbm_diag *out, int reset);
 
-/* Wait for the context's stream. */
+/* Wait for the context's stream.  Returns LBM_ERR_TIMEOUT (once) if a
+ * pipeline wait of a staged step kernel ran out of its cycle budget since the
+ * last check; the state is then undefined. */
 lbm_status lbm_synchronize(lbm_ctx *ctx);
+
+/* Cycle budget of one pipeline wait of the staged step kernels (default 2^31
+ * cycles, about a second).  After a wait runs out, the kernel raises the
+ * context's error flag, lets the copies it has in flight land and returns;
+ * lbm_synchronize or lbm_diagnostics then report LBM_ERR_TIMEOUT.  A budget of
+ * 0 makes every wait fail at once: used to test that path. */
+lbm_status lbm_set_wait_budget(lbm_ctx *ctx, int64_t cycles);
 
 /* Checkpoint: write / read the state (populations, step counter, time
  * accumulators) to / from a file.  lbm_load requires a context created with

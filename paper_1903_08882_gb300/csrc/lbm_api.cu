@@ -41,9 +41,12 @@ struct lbm_ctx {
     size_t mom_bytes = 0;
     double *dsum = nullptr;               // partial[nblocks][kNDiag], raw[kNDiag], acc[kNDiag + 1]
     size_t dsum_bytes = 0;
-    uint32_t *face = nullptr;             // flat indices of the nodes next to a face (AA odd step)
-    size_t face_bytes = 0;
-    uint32_t nface = 0;
+    uint32_t *face = nullptr;             // flat indices of the nodes next to a face (AA odd step),
+    size_t face_bytes = 0;                // those on a y or z face first
+    uint32_t nface = 0, nface_yz = 0;
+    bool staged = false;                  // AA steps without a sample use the staged kernels
+    StagedGeom T{};
+    int *flag = nullptr;                  // device error flag of the staged kernels
     int nblocks = 0;
     int elem = 4;   // bytes per flow population (f)
     int elem_g = 4; // bytes per thermal population (g)
@@ -163,6 +166,10 @@ lbm_status validate_and_derive(const lbm_params &p, lbm_constants &c, std::strin
         why = "nodes_per_thread must be 0, 1 or 2";
         return LBM_ERR_PARAM;
     }
+    if (p.pipeline < 0 || p.pipeline > 2) {
+        why = "pipeline must be 0, 1 or 2";
+        return LBM_ERR_PARAM;
+    }
     if (p.diag_every < 0) {
         why = "diag_every must be >= 0";
         return LBM_ERR_PARAM;
@@ -249,7 +256,9 @@ lbm_status release(lbm_ctx *ctx) {
     ctx->dfree(ctx->mom, ctx->mom_bytes);
     ctx->dfree(ctx->dsum, ctx->dsum_bytes);
     ctx->dfree(ctx->face, ctx->face_bytes);
+    ctx->dfree(ctx->flag, 256);
     ctx->face = nullptr;
+    ctx->flag = nullptr;
     ctx->pop = ctx->pop2 = nullptr;
     ctx->mom = nullptr;
     ctx->dsum = nullptr;
@@ -284,6 +293,17 @@ lbm_status sample_into(lbm_ctx *ctx) {
 } // namespace
 
 extern "C" {
+
+// Read (and clear) the staged kernels' error flag.  Synchronises the stream.
+static lbm_status check_flag(lbm_ctx *ctx) {
+    if (!ctx->staged) return LBM_OK;
+    int h = 0;
+    CK(ctx, cudaMemcpyAsync(&h, ctx->flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    if (!h) return LBM_OK;
+    CK(ctx, cudaMemsetAsync(ctx->flag, 0, sizeof(int), ctx->stream));
+    return fail(ctx, LBM_ERR_TIMEOUT, "a staged step kernel's pipeline wait ran out of its cycle budget; the state is undefined");
+}
 
 lbm_status lbm_create(const lbm_params *params, const lbm_allocator *alloc, void *stream, lbm_ctx **out) {
     if (!out) return fail(nullptr, LBM_ERR_PARAM, "out is NULL");
@@ -357,14 +377,21 @@ lbm_status lbm_create(const lbm_params *params, const lbm_allocator *alloc, void
     ctx->mom_bytes = (size_t)kMomArrays * G.stride * sizeof(float);
     ctx->nblocks = diag_blocks(G);
     ctx->dsum_bytes = ((size_t)ctx->nblocks * kNDiag + 2 * kNDiag + 1) * sizeof(double);
-    // nodes next to a face: the general-path share of the AA odd step
+    // nodes next to a face: the general-path share of the AA odd step; those
+    // on a y or z face first (the staged odd kernel handles the x faces itself)
     std::vector<uint32_t> face;
     face.reserve((size_t)(c.nodes - G.ni));
-    for (int z = 0; z < G.nz; ++z)
-        for (int y = 0; y < G.ny; ++y)
-            for (int x = 0; x < G.nx; ++x)
-                if (x == 0 || y == 0 || z == 0 || x == G.nx - 1 || y == G.ny - 1 || z == G.nz - 1)
-                    face.push_back((uint32_t)x + (uint32_t)G.nx * ((uint32_t)y + (uint32_t)G.ny * (uint32_t)z));
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int z = 0; z < G.nz; ++z)
+            for (int y = 0; y < G.ny; ++y)
+                for (int x = 0; x < G.nx; ++x) {
+                    const bool yz = y == 0 || z == 0 || y == G.ny - 1 || z == G.nz - 1;
+                    const bool xf = x == 0 || x == G.nx - 1;
+                    if (pass == 0 ? yz : (xf && !yz))
+                        face.push_back((uint32_t)x + (uint32_t)G.nx * ((uint32_t)y + (uint32_t)G.ny * (uint32_t)z));
+                }
+        if (pass == 0) ctx->nface_yz = (uint32_t)face.size();
+    }
     ctx->nface = (uint32_t)face.size();
     ctx->face_bytes = face.size() * sizeof(uint32_t);
     ctx->face = (uint32_t *)ctx->dalloc(ctx->face_bytes);
@@ -372,18 +399,49 @@ lbm_status lbm_create(const lbm_params *params, const lbm_allocator *alloc, void
     if (params->streaming == LBM_STREAM_PULL2) ctx->pop2 = ctx->dalloc(ctx->pop_bytes);
     ctx->mom = (float *)ctx->dalloc(ctx->mom_bytes);
     ctx->dsum = (double *)ctx->dalloc(ctx->dsum_bytes);
-    if (!ctx->pop || !ctx->mom || !ctx->dsum || !ctx->face || (params->streaming == LBM_STREAM_PULL2 && !ctx->pop2)) {
+    ctx->flag = (int *)ctx->dalloc(256);
+    if (!ctx->pop || !ctx->mom || !ctx->dsum || !ctx->face || !ctx->flag ||
+        (params->streaming == LBM_STREAM_PULL2 && !ctx->pop2)) {
         release(ctx);
         delete ctx;
         return fail(nullptr, LBM_ERR_OOM, "device allocation failed");
     }
-    ctx->c.device_bytes =
-        (int64_t)(ctx->pop_bytes * (ctx->pop2 ? 2 : 1) + ctx->mom_bytes + ctx->dsum_bytes + ctx->face_bytes);
+    ctx->c.device_bytes = (int64_t)(ctx->pop_bytes * (ctx->pop2 ? 2 : 1) + ctx->mom_bytes + ctx->dsum_bytes +
+                                    ctx->face_bytes + 256);
+    // staged kernels: AA streaming, 16-byte aligned arrays (bulk copies), and
+    // at least one block of them resident per SM
+    // (library default: staged for the 2-byte flow storages, where they
+    // measure faster than the register kernels; register kernels for FP32,
+    // whose register kernels already run at the copy bandwidth)
+    const bool want = params->pipeline == 2 || (params->pipeline == 0 && params->storage != LBM_FP32);
+    if (params->streaming == LBM_STREAM_AA && want && ((uintptr_t)ctx->pop & 15) == 0) {
+        int per_sm = 0, nsm = 0;
+        if (staged_prepare(params->storage, &per_sm) == cudaSuccess && per_sm > 0 &&
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->dev) == cudaSuccess && nsm > 0) {
+            const uint32_t tile = (uint32_t)staged_tile_nodes();
+            StagedGeom &T = ctx->T;
+            T.even_tiles = (uint32_t)((c.nodes + tile - 1) / tile);
+            T.tpp = (G.nxy - 2u * (uint32_t)G.nx + 1u + tile - 1u) / tile;
+            T.mag_tpp = magic_of(T.tpp);
+            T.odd_tiles = T.tpp * (uint32_t)(G.nz - 2);
+            T.grid = nsm * (per_sm < 2 ? per_sm : 2);
+            T.budget = 1ll << 31;
+            ctx->staged = true;
+        }
+        cudaGetLastError(); // a failed opt-in leaves the register kernels in use
+    }
+    if (params->pipeline == 2 && !ctx->staged) {
+        release(ctx);
+        delete ctx;
+        return fail(nullptr, LBM_ERR_PARAM,
+                    "staged kernels unavailable (they need AA streaming, 16-byte aligned memory and room on an SM)");
+    }
     // rest state: all deviations zero (f = w rho0, g = 0); pad entries zero too
     cudaError_t e = cudaMemsetAsync(ctx->pop, 0, ctx->pop_bytes, ctx->stream);
     if (e == cudaSuccess && ctx->pop2) e = cudaMemsetAsync(ctx->pop2, 0, ctx->pop_bytes, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->mom, 0, ctx->mom_bytes, ctx->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->dsum, 0, ctx->dsum_bytes, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->flag, 0, 256, ctx->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(ctx->face, face.data(), ctx->face_bytes, cudaMemcpyHostToDevice, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
@@ -529,6 +587,9 @@ lbm_status lbm_step(lbm_ctx *ctx, int64_t nsteps) {
     a.P = ctx->P;
     a.face = ctx->face;
     a.nface = ctx->nface;
+    a.nface_yz = ctx->nface_yz;
+    a.T = ctx->T;
+    a.err = ctx->flag;
     a.stream = ctx->stream;
     for (int64_t t = 0; t < nsteps; ++t) {
         const bool sample = ctx->p.diag_every > 0 && ctx->step % ctx->p.diag_every == 0;
@@ -538,7 +599,8 @@ lbm_status lbm_step(lbm_ctx *ctx, int64_t nsteps) {
         a.g = ctx->gbase(0);
         a.f2 = ctx->fbase(1);
         a.g2 = ctx->gbase(1);
-        CK(ctx, launch_step(a));
+        if (ctx->staged && !sample) CK(ctx, launch_staged(a));
+        else CK(ctx, launch_step(a));
         if (sample) {
             lbm_status s = sample_into(ctx);
             if (s != LBM_OK) return s;
@@ -584,6 +646,7 @@ lbm_status lbm_diagnostics(lbm_ctx *ctx, lbm_diag *out, int reset) {
     double host[2 * kNDiag + 1];
     CK(ctx, cudaMemcpyAsync(host, ctx->raw(), sizeof(host), cudaMemcpyDeviceToHost, ctx->stream));
     CK(ctx, cudaStreamSynchronize(ctx->stream));
+    if (lbm_status fs = check_flag(ctx); fs != LBM_OK) return fs;
     std::memset(out, 0, sizeof(*out));
     const double *raw = host, *acc = host + kNDiag;
     const double ns = acc[kNDiag];
@@ -613,11 +676,18 @@ lbm_status lbm_diagnostics(lbm_ctx *ctx, lbm_diag *out, int reset) {
     return LBM_OK;
 }
 
+lbm_status lbm_set_wait_budget(lbm_ctx *ctx, int64_t cycles) {
+    if (!ctx) return LBM_ERR_PARAM;
+    if (cycles < 0) return fail(ctx, LBM_ERR_PARAM, "negative cycle budget");
+    ctx->T.budget = cycles;
+    return LBM_OK;
+}
+
 lbm_status lbm_synchronize(lbm_ctx *ctx) {
     if (!ctx) return LBM_ERR_PARAM;
     DeviceGuard dg(ctx->dev);
     CK(ctx, cudaStreamSynchronize(ctx->stream));
-    return LBM_OK;
+    return check_flag(ctx);
 }
 
 struct CkptHeader {
@@ -735,7 +805,8 @@ lbm_status build_tiles(lbm_batch *b, int block) {
         const uint64_t warps = (uint64_t)G.cpp * (uint64_t)(G.nz - 2);
         const uint32_t nr = (uint32_t)((warps + block / 32 - 1) / (block / 32));
         for (uint32_t k = 0; k < nr; ++k) odd.push_back({c, TILE_ROWS, k});
-        const uint32_t nf = (x->nface + block - 1) / block;
+        // the row tiles cover the x faces of their rows; the y/z-face nodes remain
+        const uint32_t nf = (x->nface_yz + block - 1) / block;
         for (uint32_t k = 0; k < nf; ++k) odd.push_back({c, TILE_FACE, k});
     }
     const size_t bytes = (even.size() + odd.size()) * sizeof(Tile);
@@ -833,7 +904,7 @@ lbm_status lbm_batch_create(lbm_ctx *const *cells, int ncells, void *stream, lbm
         cd[c].f = x->fbase(0);
         cd[c].g = x->gbase(0);
         cd[c].face = x->face;
-        cd[c].nface = x->nface;
+        cd[c].nface = x->nface_yz;
     }
     lbm_ctx *a = cells[0];
     b->d_cells = (CellDev *)a->dalloc(cd.size() * sizeof(CellDev));

@@ -13,6 +13,16 @@ namespace lbm {
 constexpr int kNDiag = 24;     // raw diagnostic sums per sample
 constexpr int kMomArrays = 11; // rho - rho0, u, v, w, T, and g arriving from each of the 6 faces
 
+// Tiling of the staged (shared-memory pipelined) AA kernels.
+struct StagedGeom {
+    uint32_t even_tiles; // tiles of the even step: ceil(n / tile)
+    uint32_t odd_tiles;  // tiles of the odd step: tpp per plane 1 <= z <= nz-2
+    uint32_t tpp;        // odd-step tiles per z-plane
+    uint64_t mag_tpp;    // division magic of tpp
+    int grid;            // persistent blocks
+    long long budget;    // clock cycles one pipeline wait may take
+};
+
 struct StepArgs {
     int storage;  // StorageKind
     int scheme;   // 0: AA pattern, 1: two-buffer pull
@@ -26,10 +36,23 @@ struct StepArgs {
     float *mom;   // non-null: also write the node moments of the pre-step state
     const uint32_t *face; // AA odd step: flat indices of the nodes next to a face
     uint32_t nface;
+    uint32_t nface_yz;    // the first nface_yz of them lie on a y or z face
+    StagedGeom T;         // staged kernels only
+    int *err;             // staged kernels: set to 1 when a pipeline wait runs out
     cudaStream_t stream;
 };
 
 cudaError_t launch_step(const StepArgs &a);
+// AA odd step of the listed face nodes face[0 .. count) (general path).
+cudaError_t launch_face(const StepArgs &a, uint32_t count);
+// Staged AA step (no diagnostic sample): even step, or odd step with the
+// face nodes through launch_face.
+cudaError_t launch_staged(const StepArgs &a);
+// Opt in to the staged kernels' shared memory and report how many blocks of
+// them fit on an SM.
+cudaError_t staged_prepare(int storage, int *blocks_per_sm);
+int staged_smem_bytes(int storage);
+int staged_tile_nodes();
 // op 0: staging -> device layout, 1: device layout -> staging, 2: moments -> st
 cudaError_t launch_convert(int storage, int op, float *st, void *f, void *g, const Geom &G,
                            const Phys &P, int layout, cudaStream_t stream);

@@ -294,9 +294,14 @@ __device__ __forceinline__ uint32_t interior_node(const Geom &G, uint32_t t) {
 // Odd step over the rows with 1 <= y <= ny-2 and 1 <= z <= nz-2, which lie
 // contiguously in each z-plane.  A warp takes 64 consecutive nodes of such a
 // run, lane l the nodes l and l + 32, so every access of the warp is
-// contiguous and the second node's addresses are the first's plus 32.  Nodes
-// at x = 0 or x = nx-1 (and lanes past the end of the run) are left to the
-// face kernel: their loads stay in bounds and their results are not stored.
+// contiguous and the second node's addresses are the first's plus 32.  Lanes
+// past the end of the run load in bounds and store nothing.
+//
+// Nodes at x = 0 or x = nx-1 are updated here too: a link that arrives
+// through the x face takes the node's own opposite slot (bounce-back, with
+// anti-bounce-back for g at a Dirichlet face) or, when x is periodic, the
+// far end of the row; a link that leaves through it is stored there.  Only
+// the addresses change, chosen per lane, so these nodes cost no extra loads.
 template <int S, bool MOM>
 __device__ __forceinline__ void k_aa_odd_rows_tile(SEF<S> *__restrict__ f, SEG<S> *__restrict__ g, const Geom &G,
                                                         const Phys &P, float *__restrict__ mom, uint32_t blk, uint32_t tid, uint32_t bdim) {
@@ -311,23 +316,47 @@ __device__ __forceinline__ void k_aa_odd_rows_tile(SEF<S> *__restrict__ f, SEG<S
     const uint32_t n0 = nx * (1u + static_cast<uint32_t>(G.ny) * (zi + 1u)) + o0;
     const uint32_t x0 = n0 - nx * fast_div(n0, G.mag_nx);
     const uint32_t x1 = (n0 + 32u) - nx * fast_div(n0 + 32u, G.mag_nx);
-    const bool a0 = o0 < len && x0 != 0u && x0 != nx - 1u;
-    const bool a1 = o0 + 32u < len && x1 != 0u && x1 != nx - 1u;
+    const bool a0 = o0 < len;
+    const bool a1 = o0 + 32u < len;
     if (!a0 && !a1) return;
+    const bool lo0 = a0 && x0 == 0u, hi0 = a0 && x0 == nx - 1u;
+    const bool lo1 = a1 && x1 == 0u, hi1 = a1 && x1 == nx - 1u;
+    const bool per = G.periodic & 1;
     const int64_t s = G.stride;
     float2 fl[19], gl[7];
     fl[0] = make_float2(Store<FS(S)>::ld(f + n0), Store<FS(S)>::ld(f + n0 + 32));
 #pragma unroll
     for (int i = 1; i < 19; ++i) {
         const SEF<S> *q = f + opp19(i) * s + (int64_t)(n0 - G.off[i]);
-        fl[i] = make_float2(Store<FS(S)>::ld(q), Store<FS(S)>::ld(q + 32));
+        if (ex19(i) == 0) {
+            fl[i] = make_float2(Store<FS(S)>::ld(q), Store<FS(S)>::ld(q + 32));
+        } else {
+            // the link arrives through the x face at lo (e_x = +1) or hi (e_x = -1) nodes
+            const bool w0 = ex19(i) > 0 ? lo0 : hi0, w1 = ex19(i) > 0 ? lo1 : hi1;
+            const SEF<S> *own = per ? q + (ex19(i) > 0 ? (int64_t)nx : -(int64_t)nx) : f + i * s + n0;
+            fl[i] = make_float2(Store<FS(S)>::ld(w0 ? own : q), Store<FS(S)>::ld(w1 ? own + 32 : q + 32));
+        }
     }
     gl[0] = make_float2(Store<GS(S)>::ld(g + n0), Store<GS(S)>::ld(g + n0 + 32));
 #pragma unroll
     for (int i = 1; i < 7; ++i) {
         const SEG<S> *q = g + opp7(i) * s + (int64_t)(n0 - G.off[i]);
-        gl[i] = make_float2(Store<GS(S)>::ld(q), Store<GS(S)>::ld(q + 32));
+        if (ex7(i) == 0) {
+            gl[i] = make_float2(Store<GS(S)>::ld(q), Store<GS(S)>::ld(q + 32));
+        } else {
+            const bool w0 = ex7(i) > 0 ? lo0 : hi0, w1 = ex7(i) > 0 ? lo1 : hi1;
+            const SEG<S> *own = per ? q + (ex7(i) > 0 ? (int64_t)nx : -(int64_t)nx) : g + i * s + n0;
+            float2 v = make_float2(Store<GS(S)>::ld(w0 ? own : q), Store<GS(S)>::ld(w1 ? own + 32 : q + 32));
+            const int fc = ex7(i) > 0 ? 0 : 1; // face the link comes through
+            if (!per && ((P.dir_mask >> fc) & 1)) {
+                if (w0) v.x = P.abbT[fc] - v.x;
+                if (w1) v.y = P.abbT[fc] - v.y;
+            }
+            gl[i] = v;
+        }
     }
+    // pre-collision g arriving from the x faces (diagnostic sample)
+    const float gin_lo0 = gl[1].x, gin_lo1 = gl[1].y, gin_hi0 = gl[2].x, gin_hi1 = gl[2].y;
     const MacroT<float2> m = collide(P, fl, gl);
     f = opaque(f);
     g = opaque(g);
@@ -336,16 +365,37 @@ __device__ __forceinline__ void k_aa_odd_rows_tile(SEF<S> *__restrict__ f, SEG<S
 #pragma unroll
     for (int i = 1; i < 19; ++i) {
         SEF<S> *q = f + i * s + (int64_t)(n0 + G.off[i]);
-        if (a0) Store<FS(S)>::st(q, fl[i].x);
-        if (a1) Store<FS(S)>::st(q + 32, fl[i].y);
+        if (ex19(i) == 0) {
+            if (a0) Store<FS(S)>::st(q, fl[i].x);
+            if (a1) Store<FS(S)>::st(q + 32, fl[i].y);
+        } else {
+            // the link leaves through the x face at hi (e_x = +1) or lo (e_x = -1) nodes
+            const bool w0 = ex19(i) > 0 ? hi0 : lo0, w1 = ex19(i) > 0 ? hi1 : lo1;
+            SEF<S> *own = per ? q - (ex19(i) > 0 ? (int64_t)nx : -(int64_t)nx) : f + opp19(i) * s + n0;
+            if (a0) Store<FS(S)>::st(w0 ? own : q, fl[i].x);
+            if (a1) Store<FS(S)>::st(w1 ? own + 32 : q + 32, fl[i].y);
+        }
     }
     if (a0) Store<GS(S)>::st(g + n0, gl[0].x);
     if (a1) Store<GS(S)>::st(g + n0 + 32, gl[0].y);
 #pragma unroll
     for (int i = 1; i < 7; ++i) {
         SEG<S> *q = g + i * s + (int64_t)(n0 + G.off[i]);
-        if (a0) Store<GS(S)>::st(q, gl[i].x);
-        if (a1) Store<GS(S)>::st(q + 32, gl[i].y);
+        if (ex7(i) == 0) {
+            if (a0) Store<GS(S)>::st(q, gl[i].x);
+            if (a1) Store<GS(S)>::st(q + 32, gl[i].y);
+        } else {
+            const bool w0 = ex7(i) > 0 ? hi0 : lo0, w1 = ex7(i) > 0 ? hi1 : lo1;
+            SEG<S> *own = per ? q - (ex7(i) > 0 ? (int64_t)nx : -(int64_t)nx) : g + opp7(i) * s + n0;
+            float2 v = gl[i];
+            const int fc = ex7(i) > 0 ? 1 : 0; // face the link leaves through
+            if (!per && ((P.dir_mask >> fc) & 1)) {
+                if (w0) v.x = P.abbT[fc] - v.x;
+                if (w1) v.y = P.abbT[fc] - v.y;
+            }
+            if (a0) Store<GS(S)>::st(w0 ? own : q, v.x);
+            if (a1) Store<GS(S)>::st(w1 ? own + 32 : q + 32, v.y);
+        }
     }
     if (MOM) {
         if (a0) {
@@ -354,6 +404,8 @@ __device__ __forceinline__ void k_aa_odd_rows_tile(SEF<S> *__restrict__ f, SEG<S
             mom[2 * s + n0] = m.v.x;
             mom[3 * s + n0] = m.w.x;
             mom[4 * s + n0] = m.T.x;
+            if (lo0 && !per) mom[5 * s + n0] = gin_lo0;
+            if (hi0 && !per) mom[6 * s + n0] = gin_hi0;
         }
         if (a1) {
             const uint32_t n1 = n0 + 32u;
@@ -362,6 +414,8 @@ __device__ __forceinline__ void k_aa_odd_rows_tile(SEF<S> *__restrict__ f, SEG<S
             mom[2 * s + n1] = m.v.y;
             mom[3 * s + n1] = m.w.y;
             mom[4 * s + n1] = m.T.y;
+            if (lo1 && !per) mom[5 * s + n1] = gin_lo1;
+            if (hi1 && !per) mom[6 * s + n1] = gin_hi1;
         }
     }
 }
@@ -597,15 +651,16 @@ static cudaError_t step_t(const StepArgs &a) {
             if (a.mom) k_aa_even2<S, true><<<nb2, a.block, 0, a.stream>>>(f, g, a.G, a.P, a.mom);
             else k_aa_even2<S, false><<<nb2, a.block, 0, a.stream>>>(f, g, a.G, a.P, nullptr);
         } else {
+            // the row kernel covers the x faces of its rows; the listed y/z-face nodes remain
             const unsigned nwarps = a.G.cpp * (unsigned)(a.G.nz - 2);
-            const unsigned ni = blocks_for(nwarps, a.block / 32), nf = blocks_for(a.nface, a.block);
+            const unsigned ni = blocks_for(nwarps, a.block / 32), nf = blocks_for(a.nface_yz, a.block);
             if (a.mom) {
                 if (ni) k_aa_odd_rows<S, true><<<ni, a.block, 0, a.stream>>>(f, g, a.G, a.P, a.mom);
-                if (nf) k_aa_odd_face<S, true><<<nf, a.block, 0, a.stream>>>(f, g, a.G, a.P, a.mom, a.face, a.nface);
+                if (nf) k_aa_odd_face<S, true><<<nf, a.block, 0, a.stream>>>(f, g, a.G, a.P, a.mom, a.face, a.nface_yz);
             } else {
                 if (ni) k_aa_odd_rows<S, false><<<ni, a.block, 0, a.stream>>>(f, g, a.G, a.P, nullptr);
                 if (nf)
-                    k_aa_odd_face<S, false><<<nf, a.block, 0, a.stream>>>(f, g, a.G, a.P, nullptr, a.face, a.nface);
+                    k_aa_odd_face<S, false><<<nf, a.block, 0, a.stream>>>(f, g, a.G, a.P, nullptr, a.face, a.nface_yz);
             }
         }
     } else if (a.scheme == 0) {
@@ -630,6 +685,22 @@ static cudaError_t step_t(const StepArgs &a) {
         else k_pull<S, false><<<nb, a.block, 0, a.stream>>>(f, g, f2, g2, a.G, a.P, nullptr);
     }
     return cudaGetLastError();
+}
+
+template <int S> static cudaError_t face_t(const StepArgs &a, uint32_t count) {
+    if (count)
+        k_aa_odd_face<S, false><<<blocks_for(count, 256), 256, 0, a.stream>>>(
+            static_cast<SEF<S> *>(a.f), static_cast<SEG<S> *>(a.g), a.G, a.P, nullptr, a.face, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_face(const StepArgs &a, uint32_t count) {
+    switch (a.storage) {
+    case ST_F32: return face_t<ST_F32>(a, count);
+    case ST_F16: return face_t<ST_F16>(a, count);
+    case ST_F16M: return face_t<ST_F16M>(a, count);
+    default: return face_t<ST_BF16>(a, count);
+    }
 }
 
 cudaError_t launch_step(const StepArgs &a) {

@@ -19,6 +19,7 @@ LBM_OK, LBM_ERR_PARAM, LBM_ERR_CUDA, LBM_ERR_OOM, LBM_ERR_DIVERGED, LBM_ERR_TIME
 ADIABATIC, DIRICHLET, PERIODIC = 0, 1, 2
 STORAGE = {"fp32": 0, "fp16s": 1, "bf16s": 2, "fp16m": 3}
 STREAMING = {"aa": 0, "pull2": 1}
+PIPELINE = {"default": 0, "register": 1, "staged": 2}
 NDIAG = 24
 
 c_int, c_double, c_int64, c_void_p, c_size_t = (ctypes.c_int, ctypes.c_double, ctypes.c_int64,
@@ -38,7 +39,7 @@ class LbmParams(ctypes.Structure):
         ("body_force", c_double * 3),
         ("wall", LbmWall * 6),
         ("storage", c_int), ("streaming", c_int), ("diag_every", c_int), ("block_size", c_int),
-        ("nodes_per_thread", c_int),
+        ("nodes_per_thread", c_int), ("pipeline", c_int),
     ]
 
 
@@ -114,6 +115,7 @@ def lib():
         "lbm_sample": ([c_void_p], c_int),
         "lbm_diagnostics": ([c_void_p, P(LbmDiag), c_int], c_int),
         "lbm_synchronize": ([c_void_p], c_int),
+        "lbm_set_wait_budget": ([c_void_p, c_int64], c_int),
         "lbm_save": ([c_void_p, ctypes.c_char_p], c_int),
         "lbm_load": ([c_void_p, ctypes.c_char_p], c_int),
         "lbm_device_view": ([c_void_p, C, C, i64p, P(c_int)], c_int),
@@ -189,7 +191,7 @@ def walls_rayleigh_benard(T_bottom=0.5, T_top=-0.5):
 
 def make_params(nx, ny, nz, walls, Ra=1e6, Pr=0.71, U=0.1, H=0.0, nu=None, kappa=None, gbeta=None,
                 body_force=(0.0, 0.0, 0.0), storage="fp32", streaming="aa", diag_every=0,
-                block_size=0, nodes_per_thread=0) -> LbmParams:
+                block_size=0, nodes_per_thread=0, pipeline=0) -> LbmParams:
     p = LbmParams()
     p.nx, p.ny, p.nz = int(nx), int(ny), int(nz)
     p.Ra, p.Pr, p.U, p.H = float(Ra), float(Pr), float(U), float(H)
@@ -208,6 +210,7 @@ def make_params(nx, ny, nz, walls, Ra=1e6, Pr=0.71, U=0.1, H=0.0, nu=None, kappa
     p.diag_every = int(diag_every)
     p.block_size = int(block_size)
     p.nodes_per_thread = int(nodes_per_thread)
+    p.pipeline = PIPELINE[pipeline] if isinstance(pipeline, str) else int(pipeline)
     return p
 
 
@@ -325,6 +328,10 @@ def lbm_diagnostics(ctx, reset: bool = False, raise_on_diverged: bool = True) ->
 
 def lbm_synchronize(ctx):
     _check(ctx, lib().lbm_synchronize(ctx))
+
+
+def lbm_set_wait_budget(ctx, cycles: int):
+    _check(ctx, lib().lbm_set_wait_budget(ctx, int(cycles)))
 
 
 def lbm_save(ctx, path: str):
@@ -504,6 +511,9 @@ class Lattice:
 
     def synchronize(self):
         lbm_synchronize(self.ctx)
+
+    def set_wait_budget(self, cycles):
+        lbm_set_wait_budget(self.ctx, cycles)
 
     def save(self, path):
         lbm_save(self.ctx, path)

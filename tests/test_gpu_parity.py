@@ -84,16 +84,26 @@ WALLS = {
 }
 
 
-@pytest.mark.parametrize("scheme", ["aa1", "aa2", "pull2"])
+SCHEMES = {  # streaming, nodes per thread, AA pipeline
+    "aa1": ("aa", 1, "register"), "aa2": ("aa", 2, "register"), "staged": ("aa", 2, "staged"),
+    "pull2": ("pull2", 2, "default"),
+}
+
+
+@pytest.mark.parametrize("scheme", list(SCHEMES))
 @pytest.mark.parametrize("walls", list(WALLS))
-@pytest.mark.parametrize("n", [(5, 6, 7), (13, 11, 12), (3, 3, 3), (34, 9, 5)])
+@pytest.mark.parametrize("n", [(5, 6, 7), (13, 11, 12), (3, 3, 3), (34, 9, 5), (45, 37, 13), (80, 7, 6),
+                               (101, 9, 5)])
 def test_random_state_steps(lbm, walls, scheme, n):
-    """AA with one and two nodes per thread, and the pull scheme."""
+    """AA register kernels with one and two nodes per thread, the staged AA
+    kernels, and the pull scheme.  45 x 37 x 13 spans several 512-node tiles
+    per plane of the staged kernels with a ragged tail; 80 x 7 x 6 and
+    101 x 9 x 5 give the two-node-per-thread row kernel, which updates the
+    x-face nodes of its rows itself, runs of several warps per row."""
     p = _orc_params(n, WALLS[walls])
     f0, g0 = _random_state(p, 3)
-    streaming = "pull2" if scheme == "pull2" else "aa"
-    npt = 1 if scheme == "aa1" else 2
-    with _lattice(lbm, n, WALLS[walls], streaming=streaming, nodes_per_thread=npt) as lat:
+    streaming, npt, pipe = SCHEMES[scheme]
+    with _lattice(lbm, n, WALLS[walls], streaming=streaming, nodes_per_thread=npt, pipeline=pipe) as lat:
         lat.set_populations(f0, g0)
         f, g = lat.populations()
         ef, eg = _rel_pop(f, g, f0, g0)
@@ -154,12 +164,17 @@ def test_cfg1_trajectory_2000_steps(lbm):
 def test_rayleigh_benard_trajectory(lbm, diag_every):
     """Rayleigh-Benard cell 24^3, Ra=1e6, Pr=7, from the seeded linear profile:
     the early trajectory (before chaos) against the oracle every 500 steps,
-    with and without diagnostic sampling inside the steps."""
+    with and without diagnostic sampling inside the steps.  The conduction
+    state is linearly unstable at this Ra (Sec. 4), so FP32 rounding
+    differences grow with the convective mode: two FP32 kernels that differ
+    only in where the compiler fuses multiply-adds land 1.0e-4 and 1.1e-4 from
+    the FP64 oracle at t = 3000.  The bound is 3e-4; a wrong term in the
+    update gives errors of order one."""
     N = 24
     p = oracle.cell(N, 1e6, 7.0, oracle.rayleigh_benard_walls())
     T0 = inputs.rb_initial_temperature(N, N, N, seed=190308882)
     fo, go = oracle.init_equilibrium(p, 1.0, np.zeros(3), T0)
-    worst = 0.0
+    worst, hist = 0.0, []
     with lbm.Lattice(N, N, N, lbm.walls_rayleigh_benard(), Ra=1e6, Pr=7.0, diag_every=diag_every) as lat:
         lat.set_fields(1.0, np.zeros(3), T0)
         for t in range(500, 3001, 500):
@@ -167,19 +182,21 @@ def test_rayleigh_benard_trajectory(lbm, diag_every):
             fo, go = oracle.run(p, fo, go, 500)
             e = _rel_fields(lat.moments(), oracle.moments(p, fo, go))
             worst = max(worst, e.max())
-    assert worst < 1e-4, worst
+            hist.append(float(e.max()))
+    assert worst < 3e-4, hist
 
 
-@pytest.mark.parametrize("npt", [1, 2])
+@pytest.mark.parametrize("kernels", ["aa1", "aa2", "staged"])
 @pytest.mark.parametrize("storage,tol", [("fp16s", 2e-3), ("bf16s", 1.6e-2), ("fp16m", 2e-3)])
-def test_reduced_storage_one_step(lbm, storage, tol, npt):
+def test_reduced_storage_one_step(lbm, storage, tol, kernels):
     n = (33, 33, 33)
     p = oracle.cell(33, 1e4, 0.71, oracle.side_heated_walls())
     f0, g0 = oracle.init_equilibrium(p, 1.0, np.zeros(3), 0.0)
     f0, g0 = oracle.run(p, f0, g0, 500)
     fo, go = oracle.run(p, f0, g0, 1)
+    _, npt, pipe = SCHEMES[kernels]
     with lbm.Lattice(*n, lbm.walls_side_heated(), Ra=1e4, Pr=0.71, storage=storage,
-                     nodes_per_thread=npt) as lat:
+                     nodes_per_thread=npt, pipeline=pipe) as lat:
         lat.set_populations(f0, g0)
         lat.step(1)
         e = _rel_fields(lat.moments(), oracle.moments(p, fo, go))
@@ -267,6 +284,56 @@ def test_checkpoint_resume_bit_identical(lbm):
             db = lat.diagnostics()
     assert np.array_equal(fa, fb) and np.array_equal(ga, gb)
     assert da["samples"] == db["samples"] and da["avg_Nu_vol"] == db["avg_Nu_vol"]
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16s"])
+def test_staged_matches_register_kernels(lbm, storage):
+    """The staged and the register AA kernels run the same collision and
+    differ only in data movement (97 x 41 x 23 cell: several tiles per plane;
+    50 steps with samples every 10).  The compiler may contract multiply-adds
+    differently in the two kernels, so agreement is asserted to accumulated
+    FP32 rounding (50 steps x ~6e-8 x a small growth factor: 1e-5; FP16:
+    one storage rounding), not bit for bit."""
+    n = (97, 41, 23)
+    p = oracle.cell(n, 1e6, 0.71, oracle.side_heated_walls())
+    f0, g0 = _random_state(p, 9, du=0.02)
+    out = []
+    for pipe in ("register", "staged"):
+        with lbm.Lattice(*n, lbm.walls_side_heated(), Ra=1e6, Pr=0.71, storage=storage, pipeline=pipe,
+                         diag_every=10) as lat:
+            lat.set_populations(f0, g0)
+            lat.step(50)
+            out.append(lat.populations())
+            d = lat.diagnostics()
+            out.append(d["avg_Nu_face"][0])
+    tol = 1e-5 if storage == "fp32" else 2e-3
+    ef, eg = _rel_pop(*out[2], *out[0])
+    assert ef < tol and eg < tol, (ef, eg)
+    assert abs(out[1] - out[3]) <= tol * abs(out[1])
+
+
+def test_staged_wait_timeout_is_reported(lbm):
+    """A zero cycle budget makes every pipeline wait of the staged kernels run
+    out: the kernels raise the error flag and return, synchronize reports
+    LBM_ERR_TIMEOUT, and the context works again once the budget is back."""
+    n = (40, 30, 20)
+    p = _orc_params(n, WALLS["side_heated"])
+    f0, g0 = _random_state(p, 4)
+    with _lattice(lbm, n, WALLS["side_heated"], pipeline="staged") as lat:
+        lat.set_populations(f0, g0)
+        lat.set_wait_budget(0)
+        lat.step(2)
+        with pytest.raises(lbm.LbmError) as ei:
+            lat.synchronize()
+        assert ei.value.status == lbm.LBM_ERR_TIMEOUT
+        lat.set_wait_budget(1 << 31)
+        lat.set_populations(f0, g0)
+        lat.step(2)
+        lat.synchronize()
+        f, g = lat.populations()
+    fo, go = oracle.run(p, f0, g0, 2)
+    ef, eg = _rel_pop(f, g, fo, go)
+    assert ef < 2e-6 and eg < 2e-6, (ef, eg)
 
 
 def test_divergence_is_reported(lbm):
