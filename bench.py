@@ -41,7 +41,12 @@ NOMINAL_HBM_GBS = 8000.0
 FALLBACK_HBM_GBS = 6800.0
 METRIC = "GLUPS (D3Q19+D3Q7) and % HBM roofline at 257^3, FP32 vs FP16 storage"
 STEP_KERNEL_SRC = [os.path.join(ROOT, "paper_1903_08882_gb300", "csrc", f)
-                   for f in ("lbm_kernels.cu", "lbm_device.cuh")]
+                   for f in ("lbm_kernels.cu", "lbm_staged.cu", "lbm_device.cuh")]
+# kernels of one LB time step with the library's default kernels per storage
+STEP_KERNELS = {
+    "fp32": "k_aa_even2 (even steps); k_aa_odd_rows + k_aa_odd_face on the y/z-face nodes (odd steps)",
+    "staged": "k_aa_staged<even> (even steps); k_aa_staged<odd> + k_aa_odd_face on the face nodes (odd steps)",
+}
 
 
 def _peak_hbm():
@@ -211,20 +216,25 @@ def _time_chunks(lat, k, stream):
     return ev0.elapsed_time(ev1) / 1e3
 
 
-def _step_kernel_seconds(lat, stream, launches=99):
-    """Average duration of the step kernel: `launches` consecutive plain step
-    launches (no diagnostic sample falls among them), bracketed by events on
-    the library's stream."""
+def _step_kernel_seconds(lat, stream, launches=98):
+    """Average duration of one LB time step's kernels: `launches` consecutive
+    plain steps (no diagnostic sample falls among them), each bracketed by
+    events on the library's stream; also the median even and odd step."""
     import torch
 
     c = lat.diagnostics(raise_on_diverged=False)["step"]
     lat.step((-c) % CHUNK + 1)  # now one past a sampling step
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    lat.step(launches)
-    ev1.record(stream)
-    ev1.synchronize()
-    return ev0.elapsed_time(ev1) / 1e3 / launches
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(launches + 1)]
+    for k in range(launches):
+        ev[k].record(stream)
+        lat.step(1)
+    ev[launches].record(stream)
+    ev[launches].synchronize()
+    t = [ev[k].elapsed_time(ev[k + 1]) / 1e3 for k in range(launches)]
+    first_even = lat.diagnostics(raise_on_diverged=False)["step"] - launches
+    even = sorted(t[(first_even % 2)::2])
+    odd = sorted(t[1 - (first_even % 2)::2])
+    return ev[0].elapsed_time(ev[launches]) / 1e3 / launches, even[len(even) // 2], odd[len(odd) // 2]
 
 
 def bench_storage(lbm, storage, args, stream, dist, with_e2e):
@@ -246,8 +256,9 @@ def bench_storage(lbm, storage, args, stream, dist, with_e2e):
         res["seconds"] = dt
         res["glups"] = nodes * CHUNK * args.steps * (dist.get_world_size() if dist else 1) / dt / 1e9
         res["clocks"] = cs.summary()
-        tk = _step_kernel_seconds(lat, stream)
+        tk, te, to = _step_kernel_seconds(lat, stream)
         res["kernel_seconds"] = tk
+        res["kernel_even_seconds"], res["kernel_odd_seconds"] = te, to
         d = lat.diagnostics(raise_on_diverged=False)
         res["Nu_hot"] = float(d["Nu_face"][0])
         res["diverged"] = bool(d["diverged"])
@@ -351,7 +362,8 @@ def run_gpu(args):
         return
     if "fp32" not in results:  # profiling run of one storage form
         for st, r in results.items():
-            print(json.dumps({"storage": st, "glups": r["glups"], "kernel_ms": r["kernel_seconds"] * 1e3}))
+            print(json.dumps({"storage": st, "glups": r["glups"], "kernel_ms": r["kernel_seconds"] * 1e3,
+                              "even_ms": r["kernel_even_seconds"] * 1e3, "odd_ms": r["kernel_odd_seconds"] * 1e3}))
         return
     main = results["fp32"]
     nodes = N_EDGE ** 3
@@ -363,8 +375,10 @@ def run_gpu(args):
                 "frac_of_nominal_8000": round(ach / NOMINAL_HBM_GBS, 4),
                 "algorithmic_bytes_per_launch": BYTES_PER_NODE[st] * nodes,
                 "traffic": _profiled_traffic(st),
-                "kernel": f"one AA LB time step, {st} storage (k_aa_even2, or k_aa_odd_rows + k_aa_odd_face)",
+                "kernel": f"one AA LB time step, {st} storage: " + STEP_KERNELS["fp32" if st == "fp32" else "staged"],
                 "kernel_ms": round(r["kernel_seconds"] * 1e3, 4),
+                "kernel_even_ms": round(r["kernel_even_seconds"] * 1e3, 4),
+                "kernel_odd_ms": round(r["kernel_odd_seconds"] * 1e3, 4),
                 "kernel_glups": round(nodes / r["kernel_seconds"] / 1e9, 3)}
 
     batched = None
@@ -385,7 +399,9 @@ def run_gpu(args):
         "roofline": roof(main, "fp32"),
         "clocks": main["clocks"],
         "e2e": main.get("e2e"),
-        "gpu_launches": (CHUNK + 2) * args.steps,
+        # per chunk: CHUNK/2 even steps (one kernel), CHUNK/2 odd steps (row or
+        # staged kernel + face kernel), one diagnostic sample (two kernels)
+        "gpu_launches": (CHUNK // 2 * 3 + 2) * args.steps,
         "cpu_baseline": ({"value": cpu_rate, "unit": "GLUPS", "cores": threads, "kind": "oracle",
                           "sample": sample} if cpu_rate else None),
         "storage_variants": {st: {"value": round(r["glups"], 3), "unit": "GLUPS",
