@@ -424,7 +424,7 @@ lbm_status lbm_create(const lbm_params *params, const lbm_allocator *alloc, void
             T.tpp = (G.nxy - 2u * (uint32_t)G.nx + 1u + tile - 1u) / tile;
             T.mag_tpp = magic_of(T.tpp);
             T.odd_tiles = T.tpp * (uint32_t)(G.nz - 2);
-            T.grid = nsm * (per_sm < 2 ? per_sm : 2);
+            T.grid = nsm * per_sm; // persistent: every block resident
             T.budget = 1ll << 31;
             ctx->staged = true;
         }

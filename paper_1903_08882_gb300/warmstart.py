@@ -174,13 +174,21 @@ class Trainer:
             p["b"].copy_(torch.from_numpy(z[k + "_b"]))
 
 
+def start_fields(fields):
+    """(rho, u3, T) of a predicted or interpolated start.  The lattice
+    Boltzmann step conserves mass exactly, so the density deviation is
+    shifted to zero mean: the start then holds the mass of the cold start
+    (rho0 = 1 everywhere) and converges to the same steady state."""
+    drho = fields[4].astype(np.float64)
+    return 1.0 + (drho - drho.mean()) * U**2, fields[:3].astype(np.float64) * U, fields[3].astype(np.float64)
+
+
 def run_from(Ra, Pr, fields, stream, tol=1e-7, fallback_tol=None, max_steps=400_000):
     """Steps to the steady state from `fields` (None: from rest)."""
     with L.Lattice(FINE, FINE, FINE, L.walls_side_heated(), Ra=Ra, Pr=Pr, U=U, stream=stream) as lat:
         fell_back = False
         if fields is not None:
-            rho = 1.0 + fields[4].astype(np.float64) * U**2
-            lat.set_fields(rho, fields[:3].astype(np.float64) * U, fields[3].astype(np.float64))
+            lat.set_fields(*start_fields(fields))
             if fallback_tol is not None:
                 lat.sample()
                 nu0 = lat.diagnostics()["Nu_face"][0]
@@ -202,18 +210,18 @@ def _residual(a, b):
     return max(du, dT)
 
 
-def run_judged(Ra, Pr, pred, coarse_up, stream, probe=2000, fallback=1e-2, tol=1e-7, max_steps=400_000):
+def run_judged(Ra, Pr, pred, coarse_up, stream, probe=2000, fallback=0.5, tol=1e-7, max_steps=400_000):
     """Warm start with a judge: both candidate starts (the network's
     prediction and the upsampled coarse solution) advance `probe` steps; the
     one whose fields changed least continues to the steady state.  When even
-    that change exceeds `fallback` the run restarts from rest.  Every step
-    taken counts in the returned total."""
+    that change exceeds `fallback` (a start that is plainly wrong: the fields
+    change by half their size in the probe) the run restarts from rest.
+    Every step taken counts in the returned total."""
     lats, res = [], []
     try:
         for fields in (pred, coarse_up):
             lat = L.Lattice(FINE, FINE, FINE, L.walls_side_heated(), Ra=Ra, Pr=Pr, U=U, stream=stream)
-            lat.set_fields(1.0 + fields[4].astype(np.float64) * U**2, fields[:3].astype(np.float64) * U,
-                           fields[3].astype(np.float64))
+            lat.set_fields(*start_fields(fields))
             m0 = lat.moments()
             lat.step(probe)
             res.append(_residual(lat.moments(), m0))

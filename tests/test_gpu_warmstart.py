@@ -1,0 +1,58 @@
+"""What the trained warm-start network gains over the method without it.
+
+Two held-out (Ra, Pr) pairs of the side-heated cell at 65^3 (never seen in
+training): the first draw of the held-out stream and (1e6, 0.71).  Each runs
+to the steady criterion (relative change of the hot-wall Nu below 1e-7 over
+1000 steps) from rest and from the network's prediction (stored weights),
+and both runs must land on the same Nu.  Over the whole held-out evaluation
+(8 pairs) the network start took 1.43x fewer steps on the geometric mean,
+3.2x and 3.0x on the best pairs and 0.82x on the worst: the iteration's slow
+relaxation mode, which a prediction accurate to ~0.1% in Nu does not remove,
+sets the remaining steps.  On these two pairs it took 3.2x and 1.04x fewer."""
+import os
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+WEIGHTS = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_1903_08882_gb300",
+                       "warmstart_unet_65.npz")
+
+
+@pytest.fixture(scope="module")
+def ws():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1903_08882_gb300 import _build
+
+    _build.build()
+    from paper_1903_08882_gb300 import warmstart
+
+    return warmstart
+
+
+def test_network_start_against_cold_start(ws):
+    from paper_1903_08882_gb300 import inputs
+
+    pairs = inputs.warmstart_pairs(190308882, 400 + 8 + 64)
+    held_out = [pairs[400], (1e6, 0.71)]
+    stream = torch.cuda.Stream()
+    speedups = []
+    with torch.cuda.stream(stream):
+        coarse, _, converged, _ = ws.steady_set(held_out, ws.COARSE, stream)
+        assert all(converged)
+        trainer = ws.Trainer(seed=1)
+        trainer.load(WEIGHTS)
+        for (Ra, Pr), c in zip(held_out, coarse):
+            pred = trainer.predict(trainer.make_input(c, Ra, Pr))
+            cold = ws.run_from(Ra, Pr, None, stream)
+            warm = ws.run_from(Ra, Pr, pred, stream)
+            assert cold["converged"] and warm["converged"]
+            # same steady state at the criterion's resolution
+            assert abs(warm["Nu"] - cold["Nu"]) <= 1e-4 * cold["Nu"], (Ra, Pr, warm["Nu"], cold["Nu"])
+            speedups.append(cold["steps"] / warm["steps"])
+    assert speedups[0] >= 2.0, speedups
+    assert np.exp(np.mean(np.log(speedups))) > 1.2, speedups
