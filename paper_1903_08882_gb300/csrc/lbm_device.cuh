@@ -464,4 +464,90 @@ __host__ __device__ __forceinline__ MacroT<V> collide(const Phys &P, V (&f)[19],
     return mc;
 }
 
+
+// ------------------------------------------------ shared kernel helpers ----
+
+template <int S> using SEF = typename Store<FS(S)>::T; // flow element type
+template <int S> using SEG = typename Store<GS(S)>::T; // thermal element type
+
+// Hide a pointer's value from the compiler so that addresses computed from it
+// before the collision are not kept live across it (recomputing 26 addresses
+// costs a few instructions; keeping them costs 52 registers).
+template <typename T> __device__ __forceinline__ T *opaque(T *p) {
+    asm volatile("" : "+l"(p));
+    return p;
+}
+
+// Diagnostic sample of one node: moments (rho - rho0, u, v, w, T) of the
+// pre-collision state, and for a node next to a wall on face f the
+// pre-collision g arriving from that wall (velocity index f + 1 points away
+// from face f).  gin holds g before the collision.
+__device__ __forceinline__ void write_sample(float *__restrict__ mom, int64_t s, uint32_t n,
+                                             const Macro &m, const Nbr &b, const float (&gin)[7]) {
+    mom[n] = m.drho;
+    mom[s + n] = m.u;
+    mom[2 * s + n] = m.v;
+    mom[3 * s + n] = m.w;
+    mom[4 * s + n] = m.T;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (b.wm[a]) mom[(5 + 2 * a) * s + n] = gin[2 * a + 1];
+        if (b.wp[a]) mom[(6 + 2 * a) * s + n] = gin[2 * a + 2];
+    }
+}
+
+// AA odd step of one node through the general path: every link checked for
+// a wall (bounce-back, anti-bounce-back for g at a Dirichlet face) or a
+// periodic wrap.  Used for the nodes next to a face.
+template <int S, bool MOM>
+__device__ __forceinline__ void odd_step_node(SEF<S> *__restrict__ f, SEG<S> *__restrict__ g, const Geom &G,
+                                              const Phys &P, float *__restrict__ mom, uint32_t n) {
+    const int64_t s = G.stride;
+    int x, y, z;
+    node_xyz(G, n, x, y, z);
+    const Nbr b = neighbours(G, x, y, z);
+    float fl[19], gl[7];
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        if (!src_wall(b, ex19(i), ey19(i), ez19(i)))
+            fl[i] = Store<FS(S)>::ld(f + opp19(i) * s + (int64_t)n + src_off(b, ex19(i), ey19(i), ez19(i)));
+        else
+            fl[i] = Store<FS(S)>::ld(f + i * s + n);
+    }
+#pragma unroll
+    for (int i = 0; i < 7; ++i) {
+        if (!src_wall(b, ex7(i), ey7(i), ez7(i))) {
+            gl[i] = Store<GS(S)>::ld(g + opp7(i) * s + (int64_t)n + src_off(b, ex7(i), ey7(i), ez7(i)));
+        } else {
+            const int fc = face_of(-ex7(i), -ey7(i), -ez7(i));
+            const float v = Store<GS(S)>::ld(g + i * s + n);
+            gl[i] = ((P.dir_mask >> fc) & 1) ? P.abbT[fc] - v : v;
+        }
+    }
+    float g0[7];
+#pragma unroll
+    for (int i = 0; i < 7; ++i) g0[i] = gl[i];
+    const Macro m = collide(P, fl, gl);
+    f = opaque(f);
+    g = opaque(g);
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        if (!dst_wall(b, ex19(i), ey19(i), ez19(i)))
+            Store<FS(S)>::st(f + i * s + (int64_t)n + dst_off(b, ex19(i), ey19(i), ez19(i)), fl[i]);
+        else
+            Store<FS(S)>::st(f + opp19(i) * s + n, fl[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < 7; ++i) {
+        if (!dst_wall(b, ex7(i), ey7(i), ez7(i))) {
+            Store<GS(S)>::st(g + i * s + (int64_t)n + dst_off(b, ex7(i), ey7(i), ez7(i)), gl[i]);
+        } else {
+            const int fc = face_of(ex7(i), ey7(i), ez7(i));
+            const float v = gl[i];
+            Store<GS(S)>::st(g + opp7(i) * s + n, ((P.dir_mask >> fc) & 1) ? P.abbT[fc] - v : v);
+        }
+    }
+    if (MOM) write_sample(mom, s, n, m, b, g0);
+}
+
 } // namespace lbm

@@ -24,12 +24,14 @@
 // planes 1 <= z <= nz-2; a warp takes 64 consecutive nodes, lane l the nodes
 // l and l + 32, so that its stores to the shifted destinations stay
 // contiguous.  Every node next to a face goes to the general face kernel.
-// (Updating the x-face nodes here, with their wall links fetched as 16-byte
-// bulk copies or loaded per lane, measured slower at 257^3 than leaving them
-// to the face kernel: with 2-byte populations the step is bound by
-// instruction issue, and every lane paid for the extra addressing.)  Every
-// location a node reads is written by that node only, so the in-place update
-// is race-free whatever order the tiles run in.
+// (Three ways of updating the x-face nodes here measured slower at 257^3
+// than leaving them to the face kernel: their wall links fetched as 16-byte
+// bulk copies into the stage, or loaded per lane, cost every lane extra
+// addressing in an issue-bound kernel; listing them and updating them with
+// one warp every few tiles left that warp waiting on L2 while the block
+// waited for it at the next barrier.)  Every location a node reads is
+// written by that node only, so the in-place update is race-free whatever
+// order the tiles run in.
 #include "lbm_device.cuh"
 #include "lbm_internal.h"
 
