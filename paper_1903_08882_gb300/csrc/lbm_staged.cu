@@ -24,12 +24,15 @@
 // planes 1 <= z <= nz-2; a warp takes 64 consecutive nodes, lane l the nodes
 // l and l + 32, so that its stores to the shifted destinations stay
 // contiguous.  Every node next to a face goes to the general face kernel.
-// (Three ways of updating the x-face nodes here measured slower at 257^3
-// than leaving them to the face kernel: their wall links fetched as 16-byte
-// bulk copies into the stage, or loaded per lane, cost every lane extra
-// addressing in an issue-bound kernel; listing them and updating them with
-// one warp every few tiles left that warp waiting on L2 while the block
-// waited for it at the next barrier.)  Every location a node reads is
+// (Four ways of updating the x-face nodes here measured slower at 257^3
+// than leaving them to the face kernel, 494 us per FP16 odd step: their wall
+// links loaded per lane before the wait (740 us), fetched as 16-byte bulk
+// copies into the stage (617 us: the copy engine takes tiny copies one by
+// one), fetched by per-thread 4-byte asynchronous copies completing on the
+// stage's barrier (510 us: the extra flags and addresses push the kernel past
+// its 128 registers into local memory), or listed and updated by one warp
+// every few tiles (549 us: that warp waits on L2 while the block waits for it
+// at the next barrier).)  Every location a node reads is
 // written by that node only, so the in-place update is race-free whatever
 // order the tiles run in.
 #include "lbm_device.cuh"
