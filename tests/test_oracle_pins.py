@@ -450,3 +450,20 @@ def test_diagnostics_closed_forms(orc):
     assert abs(d["Re_rms"] - np.sqrt((ux**2).mean()) * N / pU.nu) < 1e-9
     assert abs(d["E"] - 0.5 * (ux**2).mean() / 0.01) < 1e-12
     assert d["rms_div"] < 1e-15 and d["Re_w"] == 0 and d["Nu_th"] == 0
+
+
+def test_paper_probe_positions_are_half_way_node_centres():
+    """Table 1 prints the probe positions of its steady side-heated runs; on an
+    N-node lattice with half-way walls (node j at (j + 1/2)/N, walls at 0 and
+    1) each is a node centre, which pins the geometry reading of the wall
+    placement (a lattice with nodes on the walls would put them at j/(N-1))."""
+    import json
+
+    ref = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_side_heated_Ra1e6.json")))
+    for key in ("81", "129"):
+        N = int(key)
+        for pos in (ref[key]["z"], ref[key]["y"]):
+            j = pos * N - 0.5
+            assert abs(j - round(j)) < 0.02, (N, pos, j)
+            k = pos * (N - 1)
+            assert abs(k - round(k)) > 0.05 or abs(j - round(j)) < abs(k - round(k)), (N, pos, k)
