@@ -64,6 +64,8 @@ def _status(L, p):
     dict(storage=7),
     dict(block_size=48),
     dict(diag_every=-1),
+    dict(pipeline=3),
+    dict(nx=1700, ny=1700, nz=1700),  # 4.9e9 nodes: beyond 32-bit node indices
 ])
 def test_invalid_parameters_rejected_on_host(L, bad):
     kw = dict(nx=8, ny=8, nz=8, walls=L.walls_side_heated(), nu=0.02, kappa=0.02, gbeta=1e-4)
