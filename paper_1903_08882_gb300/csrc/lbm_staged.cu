@@ -32,7 +32,10 @@
 // stage's barrier (510 us: the extra flags and addresses push the kernel past
 // its 128 registers into local memory), or listed and updated by one warp
 // every few tiles (549 us: that warp waits on L2 while the block waits for it
-// at the next barrier).)  Every location a node reads is
+// at the next barrier).  Scheduling the face kernel's x-face work as items of
+// this kernel, right after the tiles whose windows hold their neighbourhood,
+// gave 490 us: the cost is the general path on strided nodes, not DRAM
+// re-reads.)  Every location a node reads is
 // written by that node only, so the in-place update is race-free whatever
 // order the tiles run in.
 #include "lbm_device.cuh"
