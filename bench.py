@@ -59,10 +59,15 @@ def _peak_hbm():
 
 
 def _kernel_hash():
+    """Hash of the step kernels' code: sources with comments and whitespace
+    removed, so that only a change of the code invalidates stored counters."""
     h = hashlib.sha256()
     for p in STEP_KERNEL_SRC:
-        with open(p, "rb") as fh:
-            h.update(fh.read())
+        with open(p) as fh:
+            src = fh.read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        h.update("".join(src.split()).encode())
     return h.hexdigest()[:16]
 
 
