@@ -106,7 +106,11 @@ def test_side_heated_against_paper_tables(lbm):
     within 0.2%, E and w_max within 0.5%, v_max within 1% (measured: 0.06%,
     0.03%, 0.20%, 0.08%, 0.39%); the probe positions, node centres, agree
     exactly.  v_max is attained twice, at heights z and 1 - z (the flow is
-    centro-symmetric), so the height is compared up to that symmetry."""
+    centro-symmetric), so the height is compared up to that symmetry.  The
+    rms density of Table 3 matches to 0.01% once the hydrostatic part of the
+    paper's temperature reference is added (below); its rms velocity
+    divergence depends on a difference stencil the paper does not state and
+    is not compared."""
     from paper_1903_08882_gb300 import drivers
 
     ref = _golden("paper_side_heated_Ra1e6.json")["81"]
@@ -126,3 +130,10 @@ def test_side_heated_against_paper_tables(lbm):
     assert abs(abs(pr["u_max"]) - ref["v_max"]) <= 1e-2 * ref["v_max"], pr
     assert abs(pr["x"] - ref["y"]) < 0.5 / N, pr
     assert min(abs(pr["z"] - ref["z"]), abs(1.0 - pr["z"] - ref["z"])) < 0.5 / N, pr
+    # Table 3's rms density: the paper's buoyancy reference T0 lies at the cold
+    # wall (temperatures in [0, 1]), whose mean buoyancy adds the linear
+    # hydrostatic profile 3 g beta (1/2) (z - H/2) to rho; here T0 is the mean
+    # temperature (walls at +-1/2).  The two parts are orthogonal (the rest is
+    # symmetric in z), so the printed value is their quadrature sum.
+    hydro = 1.5 * U**2 * math.sqrt((N * N - 1) / (12.0 * N * N))
+    assert abs(math.hypot(d["rms_drho"], hydro) - ref["rms_drho"]) <= 1e-3 * ref["rms_drho"], d["rms_drho"]
