@@ -212,7 +212,8 @@ lbm_status lbm_diagnostics(lbm_ctx *ctx, lbm_diag *out, int reset);
 
 /* Wait for the context's stream.  Returns LBM_ERR_TIMEOUT (once) if a
  * pipeline wait of a staged step kernel ran out of its cycle budget since the
- * last check; the state is then undefined. */
+ * last check; the state is then undefined.  lbm_diagnostics, lbm_moments and
+ * the population readers make the same check after their data arrives. */
 lbm_status lbm_synchronize(lbm_ctx *ctx);
 
 /* Cycle budget of one pipeline wait of the staged step kernels (default 2^31

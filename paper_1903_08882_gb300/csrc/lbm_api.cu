@@ -537,6 +537,7 @@ lbm_status lbm_get_populations(lbm_ctx *ctx, double *f19, double *g7) {
     if (!host) return fail(ctx, LBM_ERR_OOM, "pinned host staging allocation failed");
     CK(ctx, cudaMemcpyAsync(host, st.ptr, (size_t)26 * n * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
     CK(ctx, cudaStreamSynchronize(ctx->stream));
+    if (lbm_status fs = check_flag(ctx); fs != LBM_OK) return fs;
     for (int i = 0; i < 19; ++i) {
         const double w = i == 0 ? 1.0 / 3.0 : (i < 7 ? 1.0 / 18.0 : 1.0 / 36.0);
         for (size_t k = 0; k < n; ++k) f19[i * n + k] = (double)host[i * n + k] + w;
@@ -564,6 +565,7 @@ lbm_status lbm_get_populations_at(lbm_ctx *ctx, const int64_t *nodes, int64_t co
     CK(ctx, cudaMemcpyAsync(host.data(), dout.ptr, host.size() * sizeof(float), cudaMemcpyDeviceToHost,
                             ctx->stream));
     CK(ctx, cudaStreamSynchronize(ctx->stream));
+    if (lbm_status fs = check_flag(ctx); fs != LBM_OK) return fs;
     for (int64_t k = 0; k < count; ++k) {
         for (int i = 0; i < 19; ++i) {
             const double w = i == 0 ? 1.0 / 3.0 : (i < 7 ? 1.0 / 18.0 : 1.0 / 36.0);
@@ -622,6 +624,7 @@ lbm_status lbm_moments(lbm_ctx *ctx, double *rho, double *u3, double *T) {
     if (!host) return fail(ctx, LBM_ERR_OOM, "pinned host staging allocation failed");
     CK(ctx, cudaMemcpyAsync(host, ctx->mom, 5 * s * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
     CK(ctx, cudaStreamSynchronize(ctx->stream));
+    if (lbm_status fs = check_flag(ctx); fs != LBM_OK) return fs;
     for (size_t k = 0; k < n; ++k) {
         rho[k] = 1.0 + (double)host[k];
         u3[k] = host[s + k];

@@ -5,10 +5,11 @@ training): the first draw of the held-out stream and (1e6, 0.71).  Each runs
 to the steady criterion (relative change of the hot-wall Nu below 1e-7 over
 1000 steps) from rest and from the network's prediction (stored weights),
 and both runs must land on the same Nu.  Over the whole held-out evaluation
-(8 pairs) the network start took 1.43x fewer steps on the geometric mean,
-3.2x and 3.0x on the best pairs and 0.82x on the worst: the iteration's slow
-relaxation mode, which a prediction accurate to ~0.1% in Nu does not remove,
-sets the remaining steps.  On these two pairs it took 3.2x and 1.04x fewer."""
+(32 pairs) the network start took 1.67x fewer steps on the geometric mean,
+up to 7.75x and 0.82x on the worst pair: the iteration's slow relaxation
+mode, which a prediction accurate to ~0.1% in Nu removes only where the
+network is most accurate, sets the remaining steps.  On these two pairs it
+took 3.24x and 1.04x fewer."""
 import os
 
 import numpy as np
