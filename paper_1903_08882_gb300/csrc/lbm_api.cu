@@ -7,8 +7,18 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/lbm.h"
 #include "lbm_internal.h"
+
+namespace {
+// Named range on the profiler timeline (NVTX; a no-op unless a tool listens).
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+};
+} // namespace
 
 using namespace lbm;
 
@@ -306,6 +316,7 @@ static lbm_status check_flag(lbm_ctx *ctx) {
 }
 
 lbm_status lbm_create(const lbm_params *params, const lbm_allocator *alloc, void *stream, lbm_ctx **out) {
+    Range range("lbm_create");
     if (!out) return fail(nullptr, LBM_ERR_PARAM, "out is NULL");
     *out = nullptr;
     if (!params) return fail(nullptr, LBM_ERR_PARAM, "params is NULL");
@@ -577,6 +588,7 @@ lbm_status lbm_get_populations_at(lbm_ctx *ctx, const int64_t *nodes, int64_t co
 }
 
 lbm_status lbm_step(lbm_ctx *ctx, int64_t nsteps) {
+    Range range("lbm_step");
     if (!ctx) return LBM_ERR_PARAM;
     if (nsteps < 0) return fail(ctx, LBM_ERR_PARAM, "negative step count");
     DeviceGuard dg(ctx->dev);
@@ -636,6 +648,7 @@ lbm_status lbm_moments(lbm_ctx *ctx, double *rho, double *u3, double *T) {
 }
 
 lbm_status lbm_sample(lbm_ctx *ctx) {
+    Range range("lbm_sample");
     if (!ctx) return LBM_ERR_PARAM;
     DeviceGuard dg(ctx->dev);
     CK(ctx, launch_convert(ctx->p.storage, 2, ctx->mom, ctx->fbase(0), ctx->gbase(0), ctx->G, ctx->P,
@@ -644,6 +657,7 @@ lbm_status lbm_sample(lbm_ctx *ctx) {
 }
 
 lbm_status lbm_diagnostics(lbm_ctx *ctx, lbm_diag *out, int reset) {
+    Range range("lbm_diagnostics");
     if (!ctx || !out) return ctx ? fail(ctx, LBM_ERR_PARAM, "out is NULL") : LBM_ERR_PARAM;
     DeviceGuard dg(ctx->dev);
     double host[2 * kNDiag + 1];
@@ -973,6 +987,7 @@ lbm_status lbm_batch_set_barrier_budget(lbm_batch *b, int64_t cycles) {
 }
 
 lbm_status lbm_batch_step(lbm_batch *b, int64_t n) {
+    Range range("lbm_batch_step");
     if (!b) return LBM_ERR_PARAM;
     if (n < 0) return bfail(b, LBM_ERR_PARAM, "negative step count");
     const int p0 = b->cells[0]->parity;

@@ -352,6 +352,26 @@ def test_divergence_is_reported(lbm):
         assert d["diverged"] and d["max_u"] > 0.5
 
 
+@pytest.mark.parametrize("pipe", ["register", "staged"])
+def test_injected_nan_is_reported(lbm, pipe):
+    """A NaN planted on the host in one node's populations spreads through the
+    steps without any fault and is reported: the next sample counts
+    non-finite nodes and lbm_diagnostics returns LBM_ERR_DIVERGED."""
+    n = (20, 18, 16)
+    p = _orc_params(n, WALLS["side_heated"])
+    f0, g0 = _random_state(p, 6)
+    f0[3, 8, 9, 10] = np.nan
+    with _lattice(lbm, n, WALLS["side_heated"], storage="fp16s", pipeline=pipe) as lat:
+        lat.set_populations(f0, g0)
+        lat.step(5)
+        lat.sample()
+        with pytest.raises(lbm.LbmError) as ei:
+            lat.diagnostics()
+        assert ei.value.status == lbm.LBM_ERR_DIVERGED
+        d = lat.diagnostics(raise_on_diverged=False)
+        assert d["diverged"] and d["nonfinite"] > 0
+
+
 def _neighbourhood_reference(p, fields, centre, k):
     """Oracle populations at `centre` after k steps from the equilibrium of
     `fields`, computed on the (2k+1)^3 box around it (clipped to the lattice)."""
