@@ -39,6 +39,22 @@ def run_to_steady(lat, every: int = 1000, tol: float = 1e-7, max_steps: int = 2_
     return dict(steps=steps, converged=False, Nu=prev, history=np.array(hist), diag=d)
 
 
+def grid_convergence(meshes, values):
+    """Grid-convergence estimate of Sec. 3 (Table 2): the asymptotic value
+    f_inf is the h = 0 value of the polynomial in h = 1/N that interpolates
+    the results on all meshes (degree = number of meshes - 1), and the order
+    n is the least-squares slope of log(|f_N - f_inf| / |f_inf|) against
+    -log N.  Returns (f_inf, n)."""
+    N = np.asarray(meshes, dtype=np.float64)
+    f = np.asarray(values, dtype=np.float64)
+    if len(N) < 3 or len(N) != len(f):
+        raise ValueError("need the same number (>= 3) of meshes and values")
+    f_inf = float(np.polyfit(1.0 / N, f, len(N) - 1)[-1])
+    err = np.abs(f - f_inf) / abs(f_inf)
+    n = float(-np.polyfit(np.log(N), np.log(err), 1)[0])
+    return f_inf, n
+
+
 def field_residuals(u_new, u_old, T_new, T_old):
     """Steady-state residuals of Sec. 3: sum |u(t+dt) - u(t)|_2 / sum |u(t)|_2
     and sum |T(t+dt) - T(t)| / sum |T(t)| over the nodes."""

@@ -467,3 +467,30 @@ def test_paper_probe_positions_are_half_way_node_centres():
             assert abs(j - round(j)) < 0.02, (N, pos, j)
             k = pos * (N - 1)
             assert abs(k - round(k)) > 0.05 or abs(j - round(j)) < abs(k - round(k)), (N, pos, k)
+
+
+def test_grid_convergence_reproduces_the_papers_table2_fits():
+    """drivers.grid_convergence applied to the Nusselt numbers the paper prints
+    for its meshes returns the f_inf and order n it prints beside them, for
+    all eight columns of Table 2 (to the printed digits)."""
+    import json
+
+    from paper_1903_08882_gb300 import drivers
+
+    ref = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_table2_convergence.json")))
+    for name, c in ref["columns"].items():
+        f_inf, n = drivers.grid_convergence(c["N"], c["f"])
+        assert abs(f_inf - c["f_inf"]) <= 1.5e-4, (name, f_inf)
+        assert abs(n - c["n"]) <= 0.006, (name, n)
+
+
+def test_grid_convergence_closed_form():
+    """On values f_inf + C N^-p (a polynomial of degree < meshes in h = 1/N
+    when p is an integer) the fit is exact."""
+    from paper_1903_08882_gb300 import drivers
+
+    N = np.array([33, 65, 129, 257])
+    for p in (1, 2, 3):
+        f = 1.25 + 7.0 * N ** -float(p)
+        f_inf, n = drivers.grid_convergence(N, f)
+        assert abs(f_inf - 1.25) < 1e-10 and abs(n - p) < 1e-6, (p, f_inf, n)
