@@ -145,23 +145,33 @@ def _dist():
     return None, 0, 1, 0
 
 
-def _max_over_ranks(dist, x):
+def _max_over_ranks(dist, x, device="cuda"):
+    """The largest of the ranks' values (the slowest rank's time)."""
     if dist is None:
         return x
     import torch
 
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
 
-def _barrier(dist):
+def _barrier(dist, cuda=True):
+    """All ranks' GPU work done and all ranks at this point."""
     import torch
 
-    torch.cuda.synchronize()
+    if cuda:
+        torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
-        torch.cuda.synchronize()
+        if cuda:
+            torch.cuda.synchronize()
+
+
+def aggregate_rate(units_per_rank, world_size, seconds):
+    """Whole-job rate of independent replicas: the units every rank processed
+    divided by the slowest rank's time (weak scaling)."""
+    return units_per_rank * world_size / seconds
 
 
 def _cpu_oracle_rate(max_seconds=15.0, min_steps=2):
@@ -259,7 +269,7 @@ def bench_storage(lbm, storage, args, stream, dist, with_e2e):
         _barrier(dist)
         dt = _max_over_ranks(dist, dt)
         res["seconds"] = dt
-        res["glups"] = nodes * CHUNK * args.steps * (dist.get_world_size() if dist else 1) / dt / 1e9
+        res["glups"] = aggregate_rate(nodes * CHUNK * args.steps, dist.get_world_size() if dist else 1, dt) / 1e9
         res["clocks"] = cs.summary()
         tk, te, to = _step_kernel_seconds(lat, stream)
         res["kernel_seconds"] = tk
@@ -298,7 +308,7 @@ def _e2e(lbm, lat, args, stream, dist):
     torch.cuda.synchronize()
     dt = _max_over_ranks(dist, time.perf_counter() - t0)
     ws = dist.get_world_size() if dist else 1
-    return {"value": N ** 3 * CHUNK * args.steps * ws / dt / 1e9, "unit": "GLUPS",
+    return {"value": aggregate_rate(N ** 3 * CHUNK * args.steps, ws, dt) / 1e9, "unit": "GLUPS",
             "h2d_bytes_per_step": 5 * 4 * N ** 3, "d2h_bytes_per_step": 8 * (2 * 24 + 1)}
 
 

@@ -79,7 +79,8 @@ def _tolerance(ref, key):
     return max(0.02, 3 * np.sqrt(2) * bm.std(ddof=1) / np.sqrt(nb) / abs(x.mean()))
 
 
-@pytest.mark.parametrize("name", ["rb_statistics_32_Ra1e6_Pr7.json", "rb_statistics_32_Ra1e5_Pr7.json"])
+@pytest.mark.parametrize("name", ["rb_statistics_32_Ra1e6_Pr7.json", "rb_statistics_32_Ra1e5_Pr7.json",
+                                  "rb_statistics_64_Ra1e6_Pr7.json"])
 @pytest.mark.parametrize("storage", ["fp32", "fp16m"])
 def test_rayleigh_benard_statistics(lbm, storage, name):
     ref = _golden(name)
