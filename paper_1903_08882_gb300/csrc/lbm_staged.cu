@@ -6,9 +6,9 @@
 //
 // Why: with 2-byte populations, a thread that loads its 26 values into
 // registers keeps too few bytes in flight to cover the HBM latency at the
-// occupancy the collision's register count allows.  Here one thread per
-// block issues the copies of the next tiles while all threads compute the
-// current one, so the loads stay in flight independently of registers.
+// occupancy the collision's register count allows.  Here one warp per block
+// issues the copies of the next tiles while all threads compute the current
+// one, so the loads stay in flight independently of registers.
 //
 // Tiles hold 512 nodes.  For each of the 26 population arrays a tile needs
 // one contiguous window: the tile's own slots on an even step, and on an odd
@@ -35,9 +35,9 @@
 // at the next barrier).  Scheduling the face kernel's x-face work as items of
 // this kernel, right after the tiles whose windows hold their neighbourhood,
 // gave 490 us: the cost is the general path on strided nodes, not DRAM
-// re-reads.)  Every location a node reads is
-// written by that node only, so the in-place update is race-free whatever
-// order the tiles run in.
+// re-reads.)
+// Every location a node reads is written by that node only, so the in-place
+// update is race-free whatever order the tiles run in.
 #include "lbm_device.cuh"
 #include "lbm_internal.h"
 
