@@ -389,7 +389,7 @@ def run_gpu(args):
                 "frac": round(ach / peak, 4), "peak_kind": peak_kind,
                 "frac_of_nominal_8000": round(ach / NOMINAL_HBM_GBS, 4),
                 "algorithmic_bytes_per_launch": BYTES_PER_NODE[st] * nodes,
-                "traffic": _profiled_traffic(st),
+                "traffic": _profiled_traffic(st) if N_EDGE == 257 else None,
                 "kernel": f"one AA LB time step, {st} storage: " + STEP_KERNELS["fp32" if st == "fp32" else "staged"],
                 "kernel_ms": round(r["kernel_seconds"] * 1e3, 4),
                 "kernel_even_ms": round(r["kernel_even_seconds"] * 1e3, 4),
@@ -409,7 +409,7 @@ def run_gpu(args):
         "data": "synthetic",
         "config": {"workload": "side-heated cube 257^3, Ra=1e7, Pr=0.71, U=0.1, FP32 storage, AA streaming",
                    "lb_steps_per_step": CHUNK, "diag_every": CHUNK, "nodes": nodes,
-                   "l2": "state (1.77 GB FP32) larger than L2, no flush",
+                   "l2": f"state ({N_EDGE ** 3 * 104 / 1e9:.2f} GB FP32) larger than L2, no flush",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
         "roofline": roof(main, "fp32"),
         "clocks": main["clocks"],

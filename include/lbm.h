@@ -91,7 +91,7 @@ typedef struct {
     int storage;    /* lbm_storage */
     int streaming;  /* lbm_streaming */
     int diag_every; /* lbm_step samples the diagnostics every diag_every steps (0: never) */
-    int block_size; /* threads per block of the step kernels, 0 = library default */
+    int block_size; /* threads per block of the register step kernels, 0 = library default (128) */
     int nodes_per_thread; /* AA step kernels: 1, or 2 (packed FP32 arithmetic); 0 = library default (2) */
     int pipeline; /* AA steps without a diagnostic sample: 1 = register kernels (each thread loads its
                      populations into registers), 2 = staged kernels (persistent blocks copy the

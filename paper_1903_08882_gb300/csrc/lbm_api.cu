@@ -338,7 +338,7 @@ lbm_status lbm_create(const lbm_params *params, const lbm_allocator *alloc, void
         delete ctx;
         return fail(nullptr, LBM_ERR_CUDA, "no CUDA device");
     }
-    ctx->block = params->block_size ? params->block_size : 256;
+    ctx->block = params->block_size ? params->block_size : 128;
     ctx->elem = params->storage == LBM_FP32 ? 4 : 2;
     ctx->elem_g = (params->storage == LBM_FP32 || params->storage == LBM_FP16M) ? 4 : 2;
 
