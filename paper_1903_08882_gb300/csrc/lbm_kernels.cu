@@ -363,7 +363,7 @@ __global__ void __launch_bounds__(256, 2) k_aa_odd_rows(SEF<S> *__restrict__ f, 
 // a cycle budget and reports it instead of waiting forever.
 
 template <int S, int BS>
-__global__ void __launch_bounds__(BS, BS == 128 ? 3 : 1)
+__global__ void __launch_bounds__(BS, BS == 128 ? 3 : 2)
     k_batch(const CellDev *__restrict__ cells, const Tile *__restrict__ even, int n_even, const Tile *__restrict__ odd,
             int n_odd, int nsteps, int parity0, GridBarrier *bar, long long budget) {
     // the current tile's cell description, staged in shared memory so that its
