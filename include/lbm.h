@@ -249,7 +249,8 @@ lbm_status lbm_device_view(lbm_ctx *ctx, void **f, void **g, int64_t *stride, in
  * captured once into a CUDA graph and replayed. */
 typedef struct lbm_batch lbm_batch;
 
-/* Schedule of the persistent launch. */
+/* Schedule of the persistent launch (a new batch starts at 256 threads, 2 blocks
+ * per SM, 100 steps per launch, 1000-step graphs). */
 typedef struct {
     int block_size;    /* 128 or 256 threads */
     int blocks_per_sm; /* resident blocks per SM (capped by occupancy); grid = SMs x this */

@@ -773,7 +773,7 @@ struct lbm_batch {
     int dev = 0;
     int nsm = 0;
     cudaStream_t stream = nullptr;
-    lbm_schedule sched{256, 1, 100, 1000};
+    lbm_schedule sched{256, 2, 100, 1000};
     long long budget = 1LL << 31;
     CellDev *d_cells = nullptr;
     Tile *d_tiles = nullptr; // even tiles, then odd tiles

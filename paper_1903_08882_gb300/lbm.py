@@ -402,7 +402,7 @@ def lbm_batch_get_schedule(batch) -> dict:
     return s.as_dict()
 
 
-def lbm_batch_set_schedule(batch, block_size=256, blocks_per_sm=1, steps_per_launch=100, graph_chunk=1000):
+def lbm_batch_set_schedule(batch, block_size=256, blocks_per_sm=2, steps_per_launch=100, graph_chunk=1000):
     s = LbmSchedule(block_size, blocks_per_sm, steps_per_launch, graph_chunk)
     _bcheck(lib().lbm_batch_set_schedule(batch, ctypes.byref(s)))
 
