@@ -199,8 +199,9 @@ def _cpu_oracle_rate(max_seconds=15.0, min_steps=2):
 
 
 def run_reference(args):
-    dist, rank, ws, _ = _dist()
-    if rank != 0:
+    # the oracle runs on the host: rank 0 alone times it, the other ranks of a
+    # multi-rank launch exit without work (no process group is needed)
+    if int(os.environ.get("RANK", "0")) != 0:
         return
     per_step, threads = [], None
     for k in range(args.warmup + args.steps):
@@ -210,7 +211,10 @@ def run_reference(args):
     value = statistics.mean(per_step)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+        "steps": args.steps, "warmup": args.warmup,
+        # one benchmark step (CHUNK LB steps of the whole cube) at the sampled rate
+        "ms_per_step": round(CHUNK * N_EDGE ** 3 / (value * 1e9) * 1e3, 1),
+        "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "side-heated cube 257^3, Ra=1e7, Pr=0.71, U=0.1 (bounded slab sample)"},
         "cpu_baseline": {"value": value, "unit": "GLUPS", "cores": threads, "kind": "oracle", "sample": sample},
