@@ -63,6 +63,28 @@ def field_residuals(u_new, u_old, T_new, T_old):
     return du, dT
 
 
+def blocking_standard_error(x, first_block: int = 8, min_blocks: int = 5) -> float:
+    """Standard error of the mean of a correlated series by blocking: the
+    series is cut into blocks of length b = first_block, 2 first_block, ...
+    while at least min_blocks blocks remain, the standard error is taken from
+    the spread of the block means for each b, and the largest is returned.
+    Once blocks are longer than the correlation time the block means are
+    independent and the estimate levels off at the true error; for shorter
+    blocks it is too small, so the maximum is the conservative choice.  Used
+    for the time averages of Sec. 4, whose samples stay correlated over many
+    free-fall times."""
+    x = np.asarray(x, dtype=np.float64)
+    se, b = 0.0, int(first_block)
+    if b < 1 or len(x) // b < min_blocks:
+        raise ValueError("series too short for the first block length")
+    while len(x) // b >= min_blocks:
+        nb = len(x) // b
+        means = x[: nb * b].reshape(nb, b).mean(axis=1)
+        se = max(se, float(means.std(ddof=1) / math.sqrt(nb)))
+        b *= 2
+    return se
+
+
 def averaged_statistics(lat, transient_steps: int, average_steps: int, diag_every: int):
     """Sec. 4 protocol: discard a transient, then average the sampled
     diagnostics over average_steps (samples every diag_every steps are taken

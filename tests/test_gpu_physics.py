@@ -83,13 +83,7 @@ def _tolerance(ref, key):
     # so the standard error of the mean is taken from block means, for block
     # lengths from 8 samples up to a fifth of the series, keeping the largest
     x = series[:, cols[key]]
-    se = 0.0
-    b = 8
-    while len(x) // b >= 5:
-        nb = len(x) // b
-        bm = x[: nb * b].reshape(nb, b).mean(axis=1)
-        se = max(se, bm.std(ddof=1) / np.sqrt(nb))
-        b *= 2
+    se = drivers.blocking_standard_error(x, first_block=8, min_blocks=5)
     return max(0.02, 3 * np.sqrt(2) * se / abs(x.mean()))
 
 
