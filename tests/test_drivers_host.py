@@ -48,3 +48,23 @@ def test_blocking_matches_the_exact_error_of_correlated_series(phi):
 def test_blocking_rejects_short_series():
     with pytest.raises(ValueError):
         drivers.blocking_standard_error(np.zeros(39), first_block=8, min_blocks=5)
+
+
+def test_resolution_reproduces_the_papers_table5():
+    """drivers.resolution with the printed Nu_vol of Table 4, a mesh of N
+    nodes over H = N (half-way walls) and the time step U/H of Ma = 0.1
+    (U = 0.1/sqrt(3)) gives every entry of Table 5 to the digits printed."""
+    import json
+    import math
+    import os
+
+    path = os.path.join(os.path.dirname(__file__), "golden", "paper_table5_resolution.json")
+    with open(path) as fh:
+        rows = json.load(fh)["rows"]
+    U = 0.1 / math.sqrt(3.0)
+    for Ra, Pr, N, nu, dg_eta, dg_etaB, dt_tau, n_bl in rows:
+        r = drivers.resolution(Ra, Pr, nu, N)
+        assert round(r["dg_over_eta"], 2) == dg_eta, (Ra, Pr, r)
+        assert round(r["dg_over_etaB"], 2) == dg_etaB, (Ra, Pr, r)
+        assert float(f"{U / N / r['tau_eta']:.3g}") == dt_tau, (Ra, Pr, r)
+        assert round(r["N_BL"]) == n_bl, (Ra, Pr, r)
