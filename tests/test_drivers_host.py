@@ -68,3 +68,20 @@ def test_resolution_reproduces_the_papers_table5():
         assert round(r["dg_over_etaB"], 2) == dg_etaB, (Ra, Pr, r)
         assert float(f"{U / N / r['tau_eta']:.3g}") == dt_tau, (Ra, Pr, r)
         assert round(r["N_BL"]) == n_bl, (Ra, Pr, r)
+
+
+def test_centerline_probes_read_the_two_centrelines():
+    """Table 1 probes on a constructed field (array order [component, z, y, x]):
+    u along the vertical centreline x = y = 1/2 and w along the horizontal
+    centreline y = z = 1/2; larger values off those lines must not count,
+    the sign of the extreme value is kept, positions are node centres."""
+    n, U = 9, 0.05
+    u3 = np.zeros((3, n, n, n))
+    u3[0][:, 4, 4] = U * np.array([0.1, 0.2, -0.3, 0.1, 0.0, 0.1, 0.25, 0.1, 0.0])
+    u3[2][4, 4, :] = U * np.array([0.0, 0.6, 0.2, 0.0, -0.1, -0.2, -0.5, -0.1, 0.0])
+    u3[0][:, 3, 4] = U  # decoys next to the centrelines
+    u3[2][4, 3, :] = 2 * U
+    u3[1] = 5 * U  # v is not probed
+    p = drivers.centerline_probes(u3, U)
+    assert p["u_max"] == pytest.approx(-0.3) and p["z"] == pytest.approx(2.5 / 9)
+    assert p["w_max"] == pytest.approx(0.6) and p["x"] == pytest.approx(1.5 / 9)
