@@ -294,6 +294,84 @@ def test_conduction_below_onset_with_buoyancy(orc):
     assert prof.argmax() in (N // 2 - 1, N // 2) and abs(prof.sum() - N) < 1e-12
 
 
+def _neutral_rayleigh(a):
+    """Rayleigh number at which a roll of wavenumber a (in units of 1/H) is
+    neutrally stable in a layer between rigid isothermal plates (the classical
+    linear stability problem of Rayleigh-Benard convection): (D^2 - a^2)^3 W =
+    -Ra a^2 W on |z| < 1/2 with W = DW = (D^2 - a^2)^2 W = 0 at the plates.
+    The even solution is a sum of cosh(q_k z) with q_k^2 - a^2 the three cube
+    roots of -Ra a^2; the plate conditions give a 3x3 determinant, purely
+    imaginary for real Ra, whose zero is found by bisection."""
+    from scipy.optimize import brentq
+
+    def det(Ra):
+        r = (Ra * a * a) ** (1.0 / 3.0)
+        taus = [-r, r * np.exp(1j * np.pi / 3), r * np.exp(-1j * np.pi / 3)]
+        q = [np.sqrt(a * a + t + 0j) for t in taus]
+        M = np.array([[np.cosh(qk / 2) for qk in q],
+                      [qk * np.sinh(qk / 2) for qk in q],
+                      [t * t * np.cosh(qk / 2) for t, qk in zip(taus, q)]])
+        return np.linalg.det(M).imag
+
+    return brentq(det, 1000.0, 3000.0, xtol=1e-9)
+
+
+def test_neutral_rayleigh_textbook_minimum():
+    """The stability solver above reproduces the textbook critical point of
+    rigid-rigid Rayleigh-Benard convection, Ra_c = 1707.76 at a_c = 3.117."""
+    from scipy.optimize import minimize_scalar
+
+    res = minimize_scalar(_neutral_rayleigh, bounds=(2.5, 3.8), method="bounded", options={"xatol": 1e-7})
+    assert abs(res.fun - 1707.76) < 0.01 and abs(res.x - 3.117) < 2e-3, res
+
+
+def _onset_rayleigh(orc, H, Pr, nu, ras=(1680.0, 1740.0)):
+    """Rayleigh number where the oracle's convection roll in a 2H x 3 x H box
+    (x, y periodic, plates at z = 0 and H held at +-1/2) neither grows nor
+    decays: the growth rate of the roll's vertical velocity, projected on
+    cos(2 pi x / 2H) so that the scheme's x-independent hydrostatic velocity
+    drops out, measured at two Rayleigh numbers and interpolated to zero."""
+    kappa = nu / Pr
+    nx = 2 * H
+    walls = _walls([P, P, P, P, D, D], (0, 0, 0, 0, 0.5, -0.5))
+    z = (np.arange(H) + 0.5) / H
+    cx = np.cos(2 * np.pi * (np.arange(nx) + 0.5) / nx)
+    td = H * H / kappa  # diffusive time in steps
+    chunk = int(td / 8)
+    rates = []
+    for Ra in ras:
+        p = orc.Params(nx, 3, H, walls, nu, kappa, Ra * nu * kappa / H**3, H, 0.1)
+        T = (0.5 - z)[:, None, None] + 1e-4 * np.sin(np.pi * z)[:, None, None] * cx[None, None, :] * np.ones((H, 3, nx))
+        f, g = orc.init_equilibrium(p, 1.0, np.zeros((3, H, 3, nx)), T)
+        t, amp = [], []
+        for k in range(24):  # three diffusive times; the faster modes are gone after the first
+            f, g = orc.run(p, f, g, chunk)
+            u = orc.moments(p, f, g)[1]
+            t.append((k + 1) * chunk / td)
+            amp.append(abs((u[2][:, 1, :] * cx[None, :]).sum()))
+        t, la = np.array(t), np.log(np.array(amp))
+        rates.append(np.polyfit(t[t > 1.0], la[t > 1.0], 1)[0])
+    assert rates[0] < 0 < rates[1], rates
+    return ras[0] - rates[0] * (ras[1] - ras[0]) / (rates[1] - rates[0])
+
+
+def test_convection_onset_at_the_critical_rayleigh_number(orc):
+    """Buoyancy (Sec. 2.2), the Dirichlet plates and both collisions together:
+    the oracle's roll of wavelength 2H sets in at the exact neutral Rayleigh
+    number of that wavenumber (a = pi: 1707.92), independently of Pr, with an
+    error that falls with the mesh at about second order (measured: 0.49% at
+    H = 8 and 0.18% at H = 12 for Pr = 1; 0.27% and 0.70% at H = 8 for
+    Pr = 0.7 and 7).  A force off by a constant factor, a plate temperature or
+    a wall position off by a node moves the onset by far more."""
+    exact = _neutral_rayleigh(np.pi)
+    assert abs(exact - 1707.922) < 0.01
+    err8 = abs(_onset_rayleigh(orc, 8, 1.0, 0.05) / exact - 1)
+    err12 = abs(_onset_rayleigh(orc, 12, 1.0, 0.05) / exact - 1)
+    assert err8 < 1e-2 and err12 < 4e-3 and err12 < err8, (err8, err12)
+    for Pr, nu in ((0.7, 0.05), (7.0, 0.1)):
+        assert abs(_onset_rayleigh(orc, 8, Pr, nu) / exact - 1) < 1e-2, Pr
+
+
 def _d3q7_transfer(kappa, k, a_T):
     """Per-mode transfer matrix of the D3Q7 scheme at rest, built here from the
     paper's definitions: A(k) = diag(exp(-i k e_x)) [I - N^-1 Q N (I - w 1^T)]."""
