@@ -74,6 +74,7 @@ def lib():
         _lib.orc_step_box.argtypes = [P, ip, ip, d, d, d, d]
         _lib.orc_run.argtypes = [P, d, d, i64]
         _lib.orc_diagnostics.argtypes = [P, d, d, d]
+        _lib.orc_local_dissipation.argtypes = [P, d, d, d, d]
     return _lib
 
 
@@ -274,6 +275,18 @@ def raw_diagnostics(p: Params, f, g):
     out = np.zeros(NDIAG)
     lib().orc_diagnostics(p.ref(), _dp(f), _dp(g), _dp(out))
     return out
+
+
+def local_dissipation(p: Params, f, g):
+    """Per-node dissipation rates eps_u = nu/2 sum_ij (d_i u_j + d_j u_i)^2 and
+    eps_T = kappa |grad T|^2 (Sec. 4), each (nz, ny, nx), same stencils as the
+    global diagnostics."""
+    sh = (p.nz, p.ny, p.nx)
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    eu, et = np.zeros(sh), np.zeros(sh)
+    lib().orc_local_dissipation(p.ref(), _dp(f), _dp(g), _dp(eu), _dp(et))
+    return eu, et
 
 
 def diagnostics(p: Params, f, g) -> dict:

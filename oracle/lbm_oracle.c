@@ -538,6 +538,53 @@ static double ddx(const orc_params *p, const double *phi, int a, int x, int y, i
     return 0.5 * (p0 - p1);
 }
 
+/* Local energy dissipation rates of a pre-collision state, per node (Sec. 4,
+ * the fields whose probability densities the paper reports):
+ *   eps_u = nu/2 sum_ij (d_i u_j + d_j u_i)^2,   eps_T = kappa |grad T|^2,
+ * with the derivative stencils of orc_diagnostics (central inside; one-sided
+ * through the wall value next to a no-slip or Dirichlet wall; zero-gradient
+ * next to an adiabatic wall).  Arrays of nx ny nz doubles, x fastest. */
+void orc_local_dissipation(const orc_params *p, const double *f, const double *g, double *eps_u,
+                           double *eps_T) {
+    const int nx = p->nx, ny = p->ny, nz = p->nz;
+    int64_t n = (int64_t)nx * ny * nz;
+    double *rho = (double *)malloc(sizeof(double) * n);
+    double *u3 = (double *)malloc(sizeof(double) * 3 * n);
+    double *T = (double *)malloc(sizeof(double) * n);
+    orc_moments(p, f, g, rho, u3, T);
+    const double zero_wall[6] = {0, 0, 0, 0, 0, 0};
+    const int all_walls[6] = {1, 1, 1, 1, 1, 1};
+    double Tw[6];
+    int t_has_value[6];
+    for (int fc = 0; fc < 6; ++fc) {
+        Tw[fc] = p->wall_T[fc];
+        t_has_value[fc] = p->wall_kind[fc] == ORC_DIRICHLET;
+    }
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                int64_t c = nidx(nx, ny, x, y, z);
+                double du[3][3]; /* du[i][j] = d u_j / d x_i */
+                for (int i = 0; i < 3; ++i)
+                    for (int j = 0; j < 3; ++j)
+                        du[i][j] = ddx(p, u3 + j * n, i, x, y, z, all_walls, zero_wall);
+                double e = 0.0, gg = 0.0;
+                for (int i = 0; i < 3; ++i) {
+                    for (int j = 0; j < 3; ++j) {
+                        double sij = du[i][j] + du[j][i];
+                        e += 0.5 * sij * sij;
+                    }
+                    double gi = ddx(p, T, i, x, y, z, t_has_value, Tw);
+                    gg += gi * gi;
+                }
+                eps_u[c] = p->nu * e;
+                eps_T[c] = p->kappa * gg;
+            }
+    free(rho);
+    free(u3);
+    free(T);
+}
+
 /* Raw diagnostic sums of a pre-collision state (all over the nx ny nz nodes):
  *  out[0]  node count
  *  out[1]  sum (rho - rho0)^2                     (rms density, Sec. 3)

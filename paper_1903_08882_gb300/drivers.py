@@ -85,6 +85,62 @@ def blocking_standard_error(x, first_block: int = 8, min_blocks: int = 5) -> flo
     return se
 
 
+def dissipation_pdf(eps, nbins: int = 200, xmax: float = 20.0, rms: float | None = None):
+    """Probability density of X = eps / eps_rms over the nodes (Sec. 4, the
+    PDFs of the kinetic and thermal dissipation rates), eps_rms = sqrt(<eps^2>)
+    unless given (a time series normalises by the rms over all its samples).
+    Returns (bin centres, density, eps_rms); the density integrates to the
+    fraction of nodes with X < xmax."""
+    e = np.asarray(eps, dtype=np.float64).ravel()
+    if rms is None:
+        rms = float(np.sqrt(np.mean(e * e)))
+    if not rms > 0:
+        raise ValueError("eps is zero everywhere")
+    edges = np.linspace(0.0, xmax, nbins + 1)
+    counts, _ = np.histogram(e / rms, bins=edges)
+    width = edges[1] - edges[0]
+    return 0.5 * (edges[1:] + edges[:-1]), counts / (e.size * width), rms
+
+
+def fit_stretched_exponential(x, pdf, x_min: float = 0.0, alphas=(0.05, 3.0)):
+    """Fit of the PDF tail to the stretched exponential of Sec. 4,
+    p(X*) = C / sqrt(X*) exp(-m X*^alpha), X* = X - X_mp, with X_mp the
+    abscissa of the most probable value.  The fit is least squares on
+    log p over the tail bins, X* > x_min, with a non-zero density: for a given
+    alpha, log p + log(X*)/2 = log C - m X*^alpha is linear in (log C, m),
+    and alpha minimises the residual.  Each bin is weighted by its density:
+    a histogram bin's log has a variance of about 1/count, so the sparse far
+    tail would otherwise dominate.  Returns C, m, alpha, X_mp and the
+    adjusted R^2 of the fit in log p (three parameters, same weights)."""
+    from scipy.optimize import minimize_scalar
+
+    x = np.asarray(x, dtype=np.float64)
+    pdf = np.asarray(pdf, dtype=np.float64)
+    x_mp = float(x[int(np.argmax(pdf))])
+    sel = (x - x_mp > x_min) & (pdf > 0)
+    xs = x[sel] - x_mp
+    y = np.log(pdf[sel]) + 0.5 * np.log(xs)
+    if xs.size < 4:
+        raise ValueError("too few tail bins to fit")
+
+    wt = pdf[sel] / pdf[sel].sum()
+    sw = np.sqrt(wt)
+
+    def solve(alpha):
+        A = np.stack([np.ones_like(xs), -xs**alpha], axis=1)
+        coef, *_ = np.linalg.lstsq(A * sw[:, None], y * sw, rcond=None)
+        return coef, float((wt * (A @ coef - y) ** 2).sum())
+
+    res = minimize_scalar(lambda a: solve(a)[1], bounds=alphas, method="bounded", options={"xatol": 1e-6})
+    (logC, m), sse = solve(res.x)
+    lp = np.log(pdf[sel])
+    sst = float((wt * (lp - (wt * lp).sum()) ** 2).sum())
+    n = xs.size
+    r2 = 1.0 - sse / sst if sst > 0 else 1.0
+    r2_adj = 1.0 - (1.0 - r2) * (n - 1) / max(n - 4, 1)
+    return dict(C=float(np.exp(logC)), m=float(m), alpha=float(res.x), x_mp=x_mp, r2_adj=float(r2_adj))
+
+
 def averaged_statistics(lat, transient_steps: int, average_steps: int, diag_every: int):
     """Sec. 4 protocol: discard a transient, then average the sampled
     diagnostics over average_steps (samples every diag_every steps are taken

@@ -530,6 +530,41 @@ def test_diagnostics_closed_forms(orc):
     assert d["rms_div"] < 1e-15 and d["Re_w"] == 0 and d["Nu_th"] == 0
 
 
+def test_local_dissipation_closed_forms(orc):
+    """Per-node eps_u = nu/2 sum_ij (d_i u_j + d_j u_i)^2 and eps_T = kappa |grad T|^2
+    (Sec. 4) on fields whose derivatives the stencils take exactly: u_x and the
+    z-profile of u_y quadratic in z and zero at both no-slip plates, T quadratic
+    in z through the two Dirichlet values (second-order stencils, central or
+    one-sided through the wall value, are exact for quadratics), and u_y varying
+    as sin(k x) along the periodic x axis (central difference sin(k) cos(k x))."""
+    nx, ny, H = 8, 3, 10
+    nu, ka = 0.03, 0.02
+    walls = _walls([P, P, P, P, D, D], (0, 0, 0, 0, 0.5, -0.5))
+    p = orc.Params(nx, ny, H, walls, nu, ka, 0.0, H, 0.1)
+    z = (np.arange(H) + 0.5)[:, None, None] * np.ones((H, ny, nx))
+    x = np.arange(nx)[None, None, :] * np.ones((H, ny, nx))
+    k, A, B = 2 * np.pi / nx, 0.01, 0.004
+    q = z * (H - z) / H**2
+    u3 = np.zeros((3, H, ny, nx))
+    u3[0] = A * q
+    u3[1] = B * np.sin(k * x) * q
+    T = 0.5 - z / H + 0.3 * z * (H - z) / H**2
+    f, g = orc.init_equilibrium(p, np.ones((H, ny, nx)), u3, T)
+    eu, et = orc.local_dissipation(p, f, g)
+    dq = (H - 2 * z) / H**2
+    d = np.zeros((3, 3) + z.shape)  # d[i, j] = d u_j / d x_i
+    d[2, 0] = A * dq
+    d[0, 1] = B * np.sin(k) * np.cos(k * x) * q
+    d[2, 1] = B * np.sin(k * x) * dq
+    strain = sum(0.5 * (d[i, j] + d[j, i]) ** 2 for i in range(3) for j in range(3))
+    assert np.allclose(eu, nu * strain, rtol=1e-10, atol=1e-18)
+    dT = -1.0 / H + 0.3 * (H - 2 * z) / H**2
+    assert np.allclose(et, ka * dT**2, rtol=1e-10, atol=1e-18)
+    # the per-node rates are the integrands of the global Nu_kin and Nu_th sums
+    r = orc.raw_diagnostics(p, f, g)
+    assert np.isclose(eu.sum() / nu, r[5], rtol=1e-12) and np.isclose(et.sum() / ka, r[6], rtol=1e-12)
+
+
 def test_paper_probe_positions_are_half_way_node_centres():
     """Table 1 prints the probe positions of its steady side-heated runs; on an
     N-node lattice with half-way walls (node j at (j + 1/2)/N, walls at 0 and
