@@ -202,6 +202,22 @@ lbm_status lbm_step(lbm_ctx *ctx, int64_t n);
  * rho = sum f, u = (sum e f + F/2)/rho, T = sum g (Sec. 2.2, 2.3). */
 lbm_status lbm_moments(lbm_ctx *ctx, double *rho, double *u3, double *T);
 
+/* Probability densities of the local dissipation rates of the current state
+ * (Sec. 4): eps_u = nu/2 sum_ij (d_i u_j + d_j u_i)^2 and eps_T = kappa |grad T|^2
+ * per node, with the derivative stencils of the diagnostics, normalised as
+ * X = eps / eps_rms.  counts_u[nbins] and counts_T[nbins] (host arrays,
+ * overwritten) receive the number of nodes with X in each of nbins equal bins
+ * on [0, xmax); nodes with X >= xmax are not counted.  rms_in[2] (host,
+ * optional) gives eps_rms for eps_u and eps_T, so that the samples of a time
+ * series share one normalisation; NULL computes sqrt(<eps^2>) of this state.
+ * rms_out[2] (host, optional) receives the values used.  A zero eps_rms
+ * counts every node in bin 0.  Synchronises the stream.  Errors:
+ * LBM_ERR_PARAM (nbins outside [1, 4096], xmax not positive, a NULL count
+ * array, a negative rms_in), LBM_ERR_OOM (device scratch), LBM_ERR_CUDA,
+ * LBM_ERR_TIMEOUT (as lbm_synchronize). */
+lbm_status lbm_dissipation_pdf(lbm_ctx *ctx, int nbins, double xmax, const double *rms_in, double *rms_out,
+                               uint64_t *counts_u, uint64_t *counts_T);
+
 /* Sample the diagnostics of the current state now (adds to the averages). */
 lbm_status lbm_sample(lbm_ctx *ctx);
 

@@ -647,6 +647,57 @@ lbm_status lbm_moments(lbm_ctx *ctx, double *rho, double *u3, double *T) {
     return LBM_OK;
 }
 
+lbm_status lbm_dissipation_pdf(lbm_ctx *ctx, int nbins, double xmax, const double *rms_in, double *rms_out,
+                               uint64_t *counts_u, uint64_t *counts_T) {
+    if (!ctx) return LBM_ERR_PARAM;
+    if (nbins < 1 || nbins > kPdfMaxBins) return fail(ctx, LBM_ERR_PARAM, "nbins must lie in [1, 4096]");
+    if (!(xmax > 0.0) || !std::isfinite(xmax)) return fail(ctx, LBM_ERR_PARAM, "xmax must be positive");
+    if (!counts_u || !counts_T) return fail(ctx, LBM_ERR_PARAM, "NULL count array");
+    if (rms_in && (!(rms_in[0] >= 0.0) || !(rms_in[1] >= 0.0)))
+        return fail(ctx, LBM_ERR_PARAM, "rms_in must be >= 0");
+    DeviceGuard dg(ctx->dev);
+    // moments of the current state into the sample arrays, as lbm_moments does
+    CK(ctx, launch_convert(ctx->p.storage, 2, ctx->mom, ctx->fbase(0), ctx->gbase(0), ctx->G, ctx->P,
+                           ctx->layout(), ctx->stream));
+    const size_t bytes = (2 + 2 * (size_t)nbins) * sizeof(double);
+    Scratch sc(ctx, bytes);
+    if (!sc.ptr) return fail(ctx, LBM_ERR_OOM, "staging allocation failed");
+    double *sums = static_cast<double *>(sc.ptr);
+    unsigned long long *counts = reinterpret_cast<unsigned long long *>(sums + 2);
+    CK(ctx, cudaMemsetAsync(sc.ptr, 0, bytes, ctx->stream));
+    const float nu = (float)ctx->c.nu, ka = (float)ctx->c.kappa;
+    double rms[2];
+    if (rms_in) {
+        rms[0] = rms_in[0];
+        rms[1] = rms_in[1];
+    } else {
+        CK(ctx, launch_eps_sq(ctx->mom, ctx->G, ctx->P, ctx->wallT, nu, ka, sums, ctx->stream));
+        double h[2];
+        CK(ctx, cudaMemcpyAsync(h, sums, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(ctx, cudaStreamSynchronize(ctx->stream));
+        rms[0] = std::sqrt(h[0] / (double)ctx->c.nodes);
+        rms[1] = std::sqrt(h[1] / (double)ctx->c.nodes);
+    }
+    const double scale_u = rms[0] > 0.0 ? nbins / (xmax * rms[0]) : 0.0;
+    const double scale_t = rms[1] > 0.0 ? nbins / (xmax * rms[1]) : 0.0;
+    CK(ctx, launch_eps_hist(ctx->mom, ctx->G, ctx->P, ctx->wallT, nu, ka, scale_u, scale_t, nbins, counts,
+                            ctx->stream));
+    std::vector<unsigned long long> host(2 * (size_t)nbins);
+    CK(ctx, cudaMemcpyAsync(host.data(), counts, host.size() * sizeof(unsigned long long),
+                            cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    if (lbm_status fs = check_flag(ctx); fs != LBM_OK) return fs;
+    for (int i = 0; i < nbins; ++i) {
+        counts_u[i] = host[i];
+        counts_T[i] = host[(size_t)nbins + i];
+    }
+    if (rms_out) {
+        rms_out[0] = rms[0];
+        rms_out[1] = rms[1];
+    }
+    return LBM_OK;
+}
+
 lbm_status lbm_sample(lbm_ctx *ctx) {
     Range range("lbm_sample");
     if (!ctx) return LBM_ERR_PARAM;

@@ -185,6 +185,112 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag_finish(const double *__re
     }
 }
 
+// Local dissipation rates (Sec. 4): eps_u = nu/2 sum_ij (d_i u_j + d_j u_i)^2
+// and eps_T = kappa |grad T|^2 of node n, with the stencils of k_diag.
+__device__ __forceinline__ void local_eps(const float *__restrict__ mom, int64_t s, const Geom &G,
+                                          const Phys &P, const WallT &W, uint32_t n, float nu,
+                                          float ka, float &eu, float &et) {
+    int x, y, z;
+    node_xyz(G, n, x, y, z);
+    const Nbr b = neighbours(G, x, y, z);
+    const float *phi[3] = {mom + s, mom + 2 * s, mom + 3 * s};
+    const float *T = mom + 4 * s;
+    float du[3][3]; // du[i][j] = d u_j / d x_i
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) du[i][j] = deriv(phi[j], n, b, i, true, 0.f, true, 0.f);
+    float e = 0.f, gg = 0.f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const float sij = du[i][j] + du[j][i];
+            e += 0.5f * sij * sij;
+        }
+        const float gi = deriv(T, n, b, i, (P.dir_mask >> (2 * i)) & 1, W.Tw[2 * i],
+                               (P.dir_mask >> (2 * i + 1)) & 1, W.Tw[2 * i + 1]);
+        gg += gi * gi;
+    }
+    eu = nu * e;
+    et = ka * gg;
+}
+
+// Pass 1 of the dissipation PDFs: sums of eps_u^2 and eps_T^2 over the nodes
+// (FP64), one atomic add per block and quantity into sums[0..1].
+__global__ void __launch_bounds__(kDiagThreads) k_eps_sq(const float *__restrict__ mom, Geom G, Phys P,
+                                                         WallT W, float nu, float ka,
+                                                         double *__restrict__ sums) {
+    __shared__ double sh[kDiagThreads / 32][2];
+    double a0 = 0.0, a1 = 0.0;
+    for (uint32_t n = blockIdx.x * blockDim.x + threadIdx.x; n < G.n; n += gridDim.x * blockDim.x) {
+        float eu, et;
+        local_eps(mom, G.stride, G, P, W, n, nu, ka, eu, et);
+        a0 += (double)eu * (double)eu;
+        a1 += (double)et * (double)et;
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    a0 = warp_sum(a0);
+    a1 = warp_sum(a1);
+    if (lane == 0) {
+        sh[wid][0] = a0;
+        sh[wid][1] = a1;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        a0 = warp_sum(lane < nw ? sh[lane][0] : 0.0);
+        a1 = warp_sum(lane < nw ? sh[lane][1] : 0.0);
+        if (lane == 0) {
+            atomicAdd(&sums[0], a0);
+            atomicAdd(&sums[1], a1);
+        }
+    }
+}
+
+// Pass 2: counts of X = eps / eps_rms in nbins equal bins on [0, xmax),
+// eps_u into counts[0..nbins), eps_T into counts[nbins..2 nbins).  Bins are
+// counted per block in shared memory (2 nbins unsigned ints) and added to the
+// global counters once per block.  A value outside [0, xmax), NaN included,
+// is not counted.
+__global__ void __launch_bounds__(kDiagThreads) k_eps_hist(const float *__restrict__ mom, Geom G, Phys P,
+                                                           WallT W, float nu, float ka, double scale_u,
+                                                           double scale_t, int nbins,
+                                                           unsigned long long *__restrict__ counts) {
+    extern __shared__ unsigned int hs[];
+    for (int i = threadIdx.x; i < 2 * nbins; i += blockDim.x) hs[i] = 0u;
+    __syncthreads();
+    const double top = (double)nbins;
+    for (uint32_t n = blockIdx.x * blockDim.x + threadIdx.x; n < G.n; n += gridDim.x * blockDim.x) {
+        float eu, et;
+        local_eps(mom, G.stride, G, P, W, n, nu, ka, eu, et);
+        const double xu = (double)eu * scale_u, xt = (double)et * scale_t;
+        if (xu >= 0.0 && xu < top) atomicAdd(&hs[(int)xu], 1u);
+        if (xt >= 0.0 && xt < top) atomicAdd(&hs[nbins + (int)xt], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 2 * nbins; i += blockDim.x)
+        if (hs[i]) atomicAdd(&counts[i], (unsigned long long)hs[i]);
+}
+
+cudaError_t launch_eps_sq(const float *mom, const Geom &G, const Phys &P, const float *wallT, float nu,
+                          float ka, double *sums, cudaStream_t stream) {
+    WallT W;
+    for (int k = 0; k < 6; ++k) W.Tw[k] = wallT[k];
+    k_eps_sq<<<diag_blocks(G), kDiagThreads, 0, stream>>>(mom, G, P, W, nu, ka, sums);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_eps_hist(const float *mom, const Geom &G, const Phys &P, const float *wallT, float nu,
+                            float ka, double scale_u, double scale_t, int nbins, unsigned long long *counts,
+                            cudaStream_t stream) {
+    WallT W;
+    for (int k = 0; k < 6; ++k) W.Tw[k] = wallT[k];
+    const size_t shmem = (size_t)2 * nbins * sizeof(unsigned int);
+    k_eps_hist<<<diag_blocks(G), kDiagThreads, shmem, stream>>>(mom, G, P, W, nu, ka, scale_u, scale_t, nbins,
+                                                               counts);
+    return cudaGetLastError();
+}
+
 int diag_blocks(const Geom &G) {
     const int64_t need = ((int64_t)G.n + kDiagThreads - 1) / kDiagThreads;
     return (int)(need < 152 * 8 ? need : 152 * 8);

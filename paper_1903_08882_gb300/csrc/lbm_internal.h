@@ -65,6 +65,15 @@ cudaError_t launch_equilibrium(float *st, const float *fields, uint32_t n, const
 // them into raw[kNDiag] (this sample) and add raw to acc[kNDiag] (time sums;
 // acc[kNDiag] counts the samples).
 int diag_blocks(const Geom &G);
+// Dissipation-rate PDFs (Sec. 4) from the moment arrays: sums of eps_u^2 and
+// eps_T^2 into sums[2] (added), and counts of eps * scale in [0, nbins) into
+// counts[2 nbins] (added; eps_u first).  nbins <= kPdfMaxBins.
+constexpr int kPdfMaxBins = 4096;
+cudaError_t launch_eps_sq(const float *mom, const Geom &G, const Phys &P, const float *wallT, float nu,
+                          float ka, double *sums, cudaStream_t stream);
+cudaError_t launch_eps_hist(const float *mom, const Geom &G, const Phys &P, const float *wallT, float nu,
+                            float ka, double scale_u, double scale_t, int nbins, unsigned long long *counts,
+                            cudaStream_t stream);
 cudaError_t launch_diag(const float *mom, const Geom &G, const Phys &P, const float *wallT,
                         double *partial, int nblocks, double *raw, double *acc, cudaStream_t stream);
 

@@ -113,6 +113,7 @@ def lib():
         "lbm_step": ([c_void_p, c_int64], c_int),
         "lbm_moments": ([c_void_p, dp, dp, dp], c_int),
         "lbm_sample": ([c_void_p], c_int),
+        "lbm_dissipation_pdf": ([c_void_p, c_int, c_double, dp, dp, P(ctypes.c_uint64), P(ctypes.c_uint64)], c_int),
         "lbm_diagnostics": ([c_void_p, P(LbmDiag), c_int], c_int),
         "lbm_synchronize": ([c_void_p], c_int),
         "lbm_set_wait_budget": ([c_void_p, c_int64], c_int),
@@ -310,6 +311,20 @@ def lbm_moments(ctx, shape):
     return rho, u3, T
 
 
+def lbm_dissipation_pdf(ctx, nbins: int = 200, xmax: float = 20.0, rms=None):
+    """Counts of X = eps/eps_rms of the local dissipation rates (Sec. 4) in nbins
+    bins on [0, xmax): returns (counts_u, counts_T, rms) with rms = (eps_u,
+    eps_T) rms used (given, or of this state)."""
+    cu = np.zeros(int(nbins), dtype=np.uint64)
+    ct = np.zeros(int(nbins), dtype=np.uint64)
+    out = np.zeros(2)
+    rin = None if rms is None else np.ascontiguousarray(rms, dtype=np.float64)
+    u64 = ctypes.POINTER(ctypes.c_uint64)
+    _check(ctx, lib().lbm_dissipation_pdf(ctx, int(nbins), float(xmax), None if rin is None else _dp(rin), _dp(out),
+                                           cu.ctypes.data_as(u64), ct.ctypes.data_as(u64)))
+    return cu, ct, (float(out[0]), float(out[1]))
+
+
 def lbm_sample(ctx):
     _check(ctx, lib().lbm_sample(ctx))
 
@@ -505,6 +520,9 @@ class Lattice:
 
     def sample(self):
         lbm_sample(self.ctx)
+
+    def dissipation_pdf(self, nbins=200, xmax=20.0, rms=None):
+        return lbm_dissipation_pdf(self.ctx, nbins, xmax, rms)
 
     def diagnostics(self, reset=False, raise_on_diverged=True):
         return lbm_diagnostics(self.ctx, reset, raise_on_diverged)

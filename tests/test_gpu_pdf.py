@@ -1,0 +1,88 @@
+"""Dissipation-rate PDFs of Sec. 4 on the GPU against the FP64 oracle.
+
+The device computes eps_u = nu/2 sum_ij (d_i u_j + d_j u_i)^2 and
+eps_T = kappa |grad T|^2 per node in FP32 from FP32 moments, the oracle in
+FP64 with the same stencils: eps agrees to ~1e-6 relative, so eps_rms does
+too (bound 1e-5), and with one normalisation the bin counts differ only for
+the nodes whose X lies within that rounding of a bin edge (a few per ten
+thousand at 0.08-wide bins; bound 2e-3 of the nodes plus 4)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1903_08882_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+A, D, P = 0, 1, 2
+WALLS = {
+    "side_heated": [(D, 0.5), (D, -0.5), (A, 0), (A, 0), (A, 0), (A, 0)],
+    "rayleigh_benard": [(A, 0), (A, 0), (A, 0), (A, 0), (D, 0.5), (D, -0.5)],
+}
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1903_08882_gb300 import _build
+    from paper_1903_08882_gb300 import lbm as L
+
+    _build.build()
+    oracle.build()
+    return L
+
+
+def _state(walls, n, seed):
+    nx, ny, nz = n
+    p = oracle.Params(nx, ny, nz, walls, 0.03, 0.02, 4e-3, float(nz), 0.1)
+    rho, u, T = inputs.random_fields((nz, ny, nx), seed, du=0.03)
+    f, g = oracle.init_equilibrium(p, rho, u, T)
+    f = f + inputs.noise(f.shape, seed, 20, 1e-4)
+    g = g + inputs.noise(g.shape, seed, 21, 1e-3)
+    return p, f, g
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16s"])
+@pytest.mark.parametrize("walls", ["side_heated", "rayleigh_benard"])
+def test_dissipation_pdf_against_oracle(lbm, walls, storage):
+    n = (45, 37, 13)
+    p, f0, g0 = _state(WALLS[walls], n, seed=11)
+    with lbm.Lattice(*n, WALLS[walls], nu=0.03, kappa=0.02, gbeta=4e-3, H=0.0, U=0.1, storage=storage) as lat:
+        lat.set_populations(f0, g0)
+        # the oracle reads the state the device holds (FP16 storage rounds it)
+        f, g = lat.populations() if storage != "fp32" else (f0, g0)
+        eu, et = oracle.local_dissipation(p, f, g)
+        rms_ref = (float(np.sqrt(np.mean(eu**2))), float(np.sqrt(np.mean(et**2))))
+        nbins, xmax = 100, 8.0
+        cu, ct, rms = lat.dissipation_pdf(nbins=nbins, xmax=xmax)
+        assert rms[0] == pytest.approx(rms_ref[0], rel=1e-5) and rms[1] == pytest.approx(rms_ref[1], rel=1e-5)
+        cu2, ct2, rms2 = lat.dissipation_pdf(nbins=nbins, xmax=xmax, rms=rms_ref)
+        assert rms2 == rms_ref
+    edges = np.linspace(0.0, xmax, nbins + 1)
+    nodes = eu.size
+    for got, e, r in ((cu2, eu, rms_ref[0]), (ct2, et, rms_ref[1])):
+        ref = np.histogram(e.ravel() / r, bins=edges)[0]
+        assert np.abs(got.astype(np.int64) - ref).sum() <= 2e-3 * nodes + 4
+        assert abs(int(got.sum()) - int((e / r < xmax).sum())) <= 2e-3 * nodes + 4
+        assert got.sum() > 0.9 * nodes  # the range holds the bulk of the distribution
+    # with its own rms the device's counts are the same up to the same rounding
+    assert np.abs(cu.astype(np.int64) - cu2.astype(np.int64)).sum() <= 2e-3 * nodes + 4
+
+
+def test_dissipation_pdf_degenerate_cases(lbm):
+    n = (9, 8, 7)
+    with lbm.Lattice(*n, WALLS["rayleigh_benard"], nu=0.03, kappa=0.02, gbeta=0.0, H=0.0, U=0.1) as lat:
+        # rest state: eps_u = 0 everywhere (zero rms: every node in bin 0); T = 0
+        # with walls at +-1/2 gives gradients only next to the plates
+        cu, ct, rms = lat.dissipation_pdf(nbins=16, xmax=4.0)
+        assert rms[0] == 0.0 and cu[0] == np.prod(n) and cu[1:].sum() == 0
+        assert rms[1] > 0 and ct.sum() == np.prod(n)
+        cu1, ct1, _ = lat.dissipation_pdf(nbins=1, xmax=1e9)
+        assert cu1[0] == np.prod(n) and ct1[0] == np.prod(n)
+        for kw in (dict(nbins=0), dict(nbins=4097), dict(xmax=0.0), dict(xmax=float("inf")),
+                   dict(rms=(-1.0, 1.0))):
+            with pytest.raises(lbm.LbmError):
+                lat.dissipation_pdf(**kw)
