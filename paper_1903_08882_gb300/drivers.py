@@ -102,6 +102,45 @@ def dissipation_pdf(eps, nbins: int = 200, xmax: float = 20.0, rms: float | None
     return 0.5 * (edges[1:] + edges[:-1]), counts / (e.size * width), rms
 
 
+def averaged_dissipation_pdf(lat, transient_steps: int, average_steps: int, every: int, nbins: int = 400,
+                             xmax: float = 40.0):
+    """Volume-and-time PDFs of the local dissipation rates (Sec. 4): after the
+    transient, one sample every `every` steps over `average_steps`, each
+    binned as eps / r0 with r0 the first sample's eps_rms; the rms over
+    volume and time, r = sqrt(<eps^2>_{V,t}), is known only at the end, and
+    the histogram of eps / r is the same histogram with its abscissa scaled
+    by r0 / r.  Returns the bin centres and densities of X = eps / r for
+    eps_u and eps_T, the two r, and the sample count."""
+    if every < 1 or average_steps < every:
+        raise ValueError("need at least one sample")
+    lat.step(int(transient_steps))
+    cu = np.zeros(nbins)
+    ct = np.zeros(nbins)
+    sq = np.zeros(2)
+    r0 = None
+    samples = 0
+    for _ in range(int(average_steps) // int(every)):
+        lat.step(int(every))
+        _, _, own = lat.dissipation_pdf(nbins=1, xmax=1e300)  # this sample's eps_rms
+        if r0 is None:
+            if not (own[0] > 0 and own[1] > 0):
+                raise ValueError("a dissipation rate is zero everywhere in the first sample")
+            r0 = own
+        u, t, _ = lat.dissipation_pdf(nbins=nbins, xmax=xmax, rms=r0)
+        cu += u
+        ct += t
+        sq += np.square(own)
+        samples += 1
+    r = np.sqrt(sq / samples)
+    nodes = int(np.prod(lat.shape))
+    out = dict(rms_u=float(r[0]), rms_T=float(r[1]), samples=samples)
+    for key, counts, k in (("u", cu, 0), ("T", ct, 1)):
+        width = xmax / nbins * r0[k] / r[k]
+        out["x_" + key] = (np.arange(nbins) + 0.5) * width
+        out["pdf_" + key] = counts / (nodes * samples * width)
+    return out
+
+
 def fit_stretched_exponential(x, pdf, x_min: float = 0.0, alphas=(0.05, 3.0)):
     """Fit of the PDF tail to the stretched exponential of Sec. 4,
     p(X*) = C / sqrt(X*) exp(-m X*^alpha), X* = X - X_mp, with X_mp the

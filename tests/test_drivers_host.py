@@ -141,3 +141,57 @@ def test_dissipation_pdf_of_an_exponential_field():
     big = exact > 1e-3
     assert np.all(np.abs(p[big] - exact[big]) < 5 * err[big] + 2e-2 * exact[big] * width)
     assert p.sum() * width == pytest.approx(np.mean(eps / rms < 5.0), rel=1e-12)
+
+
+class _FakeLattice:
+    """Stands in for lbm.Lattice in the time-averaging logic: each step draws
+    new exponential dissipation fields whose mean changes from sample to
+    sample, and dissipation_pdf follows the C ABI: counts of eps * nbins /
+    (xmax * rms) in [0, nbins), rms the given one or sqrt(<eps^2>)."""
+
+    def __init__(self, shape, means, seed=0):
+        self.shape = shape
+        self.means = means
+        self.rng = np.random.default_rng(seed)
+        self.k = -1
+        self.eps = None
+
+    def step(self, n):
+        self.k += 1
+        n_nodes = int(np.prod(self.shape))
+        mu_u, mu_t = self.means[self.k % len(self.means)]
+        self.eps = (self.rng.exponential(mu_u, n_nodes), self.rng.exponential(mu_t, n_nodes))
+
+    def dissipation_pdf(self, nbins=200, xmax=20.0, rms=None):
+        own = tuple(float(np.sqrt(np.mean(e * e))) for e in self.eps)
+        use = own if rms is None else tuple(rms)
+        out = []
+        for e, r in zip(self.eps, use):
+            x = e * (nbins / (xmax * r)) if r > 0 else np.zeros_like(e)
+            keep = (x >= 0) & (x < nbins)
+            out.append(np.bincount(x[keep].astype(np.int64), minlength=nbins)[:nbins].astype(np.uint64))
+        return out[0], out[1], use
+
+
+def test_averaged_dissipation_pdf_rescales_to_the_rms_over_volume_and_time():
+    """Samples with exponential eps of means mu_k: <eps^2> = 2 mu_k^2 per
+    sample, r^2 = mean_k 2 mu_k^2, and X = eps/r has the mixture density
+    mean_k (r/mu_k) exp(-X r/mu_k); the averaged histogram, binned in units
+    of the first sample's rms and rescaled, follows it."""
+    means = [(1e-5, 2e-4), (2e-5, 1e-4), (1.5e-5, 3e-4)]
+    lat = _FakeLattice((40, 50, 50), means, seed=4)
+    out = drivers.averaged_dissipation_pdf(lat, 10, 60, 10, nbins=300, xmax=30.0)
+    assert out["samples"] == 6
+    for key, k in (("u", 0), ("T", 1)):
+        mu = np.array([m[k] for m in means])
+        r = np.sqrt(np.mean(2 * mu**2))
+        assert out["rms_" + key] == pytest.approx(r, rel=1e-2)
+        x, p = out["x_" + key], out["pdf_" + key]
+        width = x[1] - x[0]
+        rr = out["rms_" + key]
+        exact = np.mean([(rr / m) * np.exp(-x * rr / m) for m in mu], axis=0)
+        n_samples = out["samples"] * 40 * 50 * 50
+        err = np.sqrt(exact / (n_samples * width))
+        big = exact > 1e-2
+        assert np.all(np.abs(p[big] - exact[big]) < 5 * err[big] + 1e-2 * exact[big])
+        assert p.sum() * width == pytest.approx(1.0, abs=1e-3)
