@@ -10,7 +10,8 @@ streaming), written from the paper's equations:
   * D3Q7 MRT with the fourth-order-isotropic rates, anti-bounce-back Dirichlet
     and bounce-back adiabatic walls (Sec. 2.3, Eq. MRT_T, Eq. magic/4th/qk/qnu),
   * the diagnostics of Sec. 3 (E, rms density and divergence, wall Nusselt
-    numbers) and Sec. 4 (Re^rms, Re_w^rms, Nu_vol, Nu_wall, Nu_kin, Nu_th).
+    numbers) and Sec. 4 (Re^rms, Re_w^rms, Nu_vol, Nu_wall, Nu_kin, Nu_th),
+  * the per-node dissipation rates eps_u and eps_T whose PDFs Sec. 4 reports.
 This module only marshals numpy arrays to it and turns raw sums into the
 paper's dimensionless numbers (free-fall units, dT = 1).
 """

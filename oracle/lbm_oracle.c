@@ -25,7 +25,9 @@
  *
  * Parity status: every function here is pinned by the CPU test suite
  * (rest state, conservation, conduction, Fourier-mode decay, Poiseuille flow,
- * BGK/TRT special cases, printed tables, symmetry and closed-form diagnostics).
+ * BGK/TRT special cases, printed tables, symmetry, the onset of convection at
+ * the exact critical Rayleigh number, and closed-form diagnostics including
+ * the per-node dissipation rates).
  */
 #include <math.h>
 #include <stdint.h>
