@@ -170,6 +170,17 @@ def _guo(t, u, F):
     return w * (3 * (e - u) @ F + 9 * (e @ u) * (e @ F))
 
 
+@pytest.mark.parametrize("H,Ra,Pr,U", [(33, 1e4, 0.71, 0.1), (257, 1e7, 0.71, 0.1 / SQ3), (64, 1e6, 7.0, 0.05)])
+def test_free_fall_scaling_definitions(orc, H, Ra, Pr, U):
+    """Sec. 2.1: with dT = 1 the free-fall velocity is U = sqrt(g beta dT H),
+    Ra = g beta dT H^3 / (nu kappa) and Pr = nu / kappa; the oracle's nu,
+    kappa and g beta must give these back."""
+    nu, ka, gb = orc.free_fall(H, Ra, Pr, U)
+    assert np.sqrt(gb * H) == pytest.approx(U, rel=1e-14)
+    assert gb * H**3 / (nu * ka) == pytest.approx(Ra, rel=1e-13)
+    assert nu / ka == pytest.approx(Pr, rel=1e-14)
+
+
 def test_bgk_limit(orc):
     """With every rate equal to 1/tau the MRT collision is BGK with Guo
     forcing: f+ = f - (f - f^eq)/tau + (1 - 1/(2 tau)) F~ (velocity space)."""
