@@ -253,3 +253,29 @@ def test_splitmix64_published_sequence():
     assert u.min() >= 0.0 and u.max() < 1.0 and abs(u.mean() - 0.5) < 0.005
     assert np.array_equal(u, inputs.uniform(190308882, 3, np.arange(100_000)))
     assert not np.array_equal(u[:100], inputs.uniform(190308882, 4, np.arange(100)))
+
+
+def test_warm_start_fields_hold_the_cold_start_mass():
+    """A predicted start (network units: u/U, v/U, w/U, T, (rho - 1)/U^2) becomes
+    lattice fields with the density deviation shifted to zero mean, so the
+    start holds exactly the mass of the rest state (the step conserves mass
+    and the steady state depends on it); velocities scale by U, T is kept."""
+    from paper_1903_08882_gb300 import warmstart as ws
+
+    pred = np.random.default_rng(2).normal(size=(5, 6, 5, 4)).astype(np.float32)
+    rho, u, T = ws.start_fields(pred)
+    assert rho.mean() == pytest.approx(1.0, abs=1e-15)
+    d = pred[4].astype(np.float64)
+    assert np.allclose(rho - 1.0, (d - d.mean()) * ws.U**2, atol=1e-15)
+    assert np.array_equal(u, pred[:3].astype(np.float64) * ws.U) and np.array_equal(T, pred[3].astype(np.float64))
+
+
+def test_warm_start_summary_statistics():
+    from paper_1903_08882_gb300 import warmstart as ws
+
+    res = [dict(speedup_network=s, speedup_judged=1.0) for s in (1.0, 2.0, 4.0, 8.0)]
+    out = ws.summarize(res)
+    n = out["speedup_network"]
+    assert n["geomean"] == pytest.approx(np.sqrt(8.0)) and n["median"] == 3.0 and n["mean"] == 3.75
+    assert n["frac_ge_3"] == 0.5 and n["n"] == 4
+    assert out["speedup_judged"]["geomean"] == 1.0 and "speedup_coarse" not in out
