@@ -76,6 +76,7 @@ def lib():
         _lib.orc_run.argtypes = [P, d, d, i64]
         _lib.orc_diagnostics.argtypes = [P, d, d, d]
         _lib.orc_local_dissipation.argtypes = [P, d, d, d, d]
+        _lib.orc_nusselt_profile.argtypes = [P, d, d, ctypes.c_int, ctypes.c_double, d]
     return _lib
 
 
@@ -288,6 +289,19 @@ def local_dissipation(p: Params, f, g):
     eu, et = np.zeros(sh), np.zeros(sh)
     lib().orc_local_dissipation(p.ref(), _dp(f), _dp(g), _dp(eu), _dp(et))
     return eu, et
+
+
+def nusselt_profile(p: Params, f, g, axis: int = 0):
+    """Plane-averaged Nusselt number along `axis` (Sec. 3, Nu(y) of Fig. 4:
+    the mean over each node plane of u_a T H / kappa - H dT/dx_a) and the
+    mid-line Nusselt numbers of the six faces (Sec. 3, Nu_mean of Table 2;
+    0 for faces that are not Dirichlet walls).  Returns (profile, nu_mid)."""
+    na = (p.nx, p.ny, p.nz)[axis]
+    f = np.ascontiguousarray(f, dtype=np.float64)
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    out = np.zeros(na + 6)
+    lib().orc_nusselt_profile(p.ref(), _dp(f), _dp(g), int(axis), float(p.H), _dp(out))
+    return out[:na], out[na:]
 
 
 def diagnostics(p: Params, f, g) -> dict:

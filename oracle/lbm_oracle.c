@@ -685,3 +685,79 @@ void orc_diagnostics(const orc_params *p, const double *f, const double *g, doub
     free(u3);
     free(T);
 }
+
+/* Nusselt numbers of Sec. 3 beyond the wall averages, of a pre-collision
+ * state, in lattice units (free-fall velocity U, wall temperature difference
+ * 1, length H).
+ *
+ * Plane-averaged profile along axis a (the x-z plane average Nu(y) of Fig. 4,
+ * taken here along any axis): for every node plane j of axis a,
+ *   out[j] = mean over the plane's nodes of (u_a T H / kappa - H dT/dx_a).
+ * The paper's integrand v T sqrt(Ra Pr) - dT/dy becomes u_a T H / kappa
+ * - H dT/dx_a with v = u_a / U, sqrt(Ra Pr) = U H / kappa and y = x_a / H;
+ * dT/dx_a uses the stencils of orc_diagnostics (central inside, one-sided
+ * through T_w next to a Dirichlet wall, zero-gradient next to an adiabatic
+ * wall).
+ *
+ * Mid-line wall Nusselt numbers (Nu_mean of Sec. 3 and Table 2), out[n_a + f]
+ * for faces f = 0..5: the mean of -H dT/dn at the wall (n into the fluid,
+ * the one-sided stencil (-8 T_w + 9 T_0 - T_1)/3 of orc_diagnostics) over
+ * the nodes next to face f on the line that runs along z (along x for the
+ * two z faces) through the middle of the third axis.  When that axis has an
+ * even number of nodes its middle lies between two node lines, and the mean
+ * is taken over both (linear interpolation to the middle).  0 for a face
+ * that is not a Dirichlet wall. */
+void orc_nusselt_profile(const orc_params *p, const double *f, const double *g, int a, double H,
+                         double *out) {
+    const int nx = p->nx, ny = p->ny, nz = p->nz;
+    const int nn[3] = {nx, ny, nz};
+    int64_t n = (int64_t)nx * ny * nz;
+    double *rho = (double *)malloc(sizeof(double) * n);
+    double *u3 = (double *)malloc(sizeof(double) * 3 * n);
+    double *T = (double *)malloc(sizeof(double) * n);
+    orc_moments(p, f, g, rho, u3, T);
+    double Tw[6];
+    int t_has_value[6];
+    for (int fc = 0; fc < 6; ++fc) {
+        Tw[fc] = p->wall_T[fc];
+        t_has_value[fc] = p->wall_kind[fc] == ORC_DIRICHLET;
+    }
+    for (int j = 0; j < nn[a]; ++j) out[j] = 0.0;
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                const int c[3] = {x, y, z};
+                int64_t i = nidx(nx, ny, x, y, z);
+                double dT = ddx(p, T, a, x, y, z, t_has_value, Tw);
+                out[c[a]] += u3[a * n + i] * T[i] * H / p->kappa - H * dT;
+            }
+    const double area = (double)n / nn[a];
+    for (int j = 0; j < nn[a]; ++j) out[j] /= area;
+    for (int fc = 0; fc < 6; ++fc) {
+        double *o = out + nn[a] + fc;
+        *o = 0.0;
+        if (p->wall_kind[fc] != ORC_DIRICHLET) continue;
+        const int b = fc / 2, hi = fc % 2;      /* normal axis */
+        const int l = b == 2 ? 0 : 2;           /* the line's axis */
+        const int m = 3 - b - l;                /* the axis whose middle the line passes through */
+        const int m0 = (nn[m] - 1) / 2, m1 = nn[m] / 2;
+        double sum = 0.0;
+        int count = 0;
+        for (int mm = m0; mm <= m1; ++mm)
+            for (int k = 0; k < nn[l]; ++k) {
+                int c0[3], c1[3];
+                c0[b] = hi ? nn[b] - 1 : 0;
+                c1[b] = hi ? nn[b] - 2 : 1;
+                c0[l] = c1[l] = k;
+                c0[m] = c1[m] = mm;
+                const double T0 = T[nidx(nx, ny, c0[0], c0[1], c0[2])];
+                const double T1 = T[nidx(nx, ny, c1[0], c1[1], c1[2])];
+                sum += -H * (-8.0 * Tw[fc] + 9.0 * T0 - T1) / 3.0;
+                count += 1;
+            }
+        *o = sum / count;
+    }
+    free(rho);
+    free(u3);
+    free(T);
+}

@@ -541,6 +541,65 @@ def test_diagnostics_closed_forms(orc):
     assert d["rms_div"] < 1e-15 and d["Re_w"] == 0 and d["Nu_th"] == 0
 
 
+def test_nusselt_profile_conduction_is_one_everywhere(orc):
+    """Sec. 3, Nu(y) of Fig. 4 and Nu_mean of Table 2: the conduction state
+    between the hot (x = 0) and cold (x = H) walls of the side-heated cell,
+    T = 1/2 - x/H at rest, carries Nu = 1 through every plane and along the
+    mid-line of both walls (the cold wall's flux points out of the fluid:
+    -1), on odd and even meshes; the adiabatic and z faces report 0."""
+    for N in (9, 10):
+        x = np.arange(N) + 0.5
+        p = orc.Params(N, N, N, _walls([D, D, A, A, A, A], (0.5, -0.5, 0, 0, 0, 0)), 0.04, 0.03, 0.0, N, 0.1)
+        T = (0.5 - x / N)[None, None, :] * np.ones((N, N, N))
+        f, g = orc.init_equilibrium(p, 1.0, np.zeros((3, N, N, N)), T)
+        prof, mid = orc.nusselt_profile(p, f, g, axis=0)
+        assert prof.shape == (N,) and np.abs(prof - 1).max() < 1e-12
+        assert abs(mid[0] - 1) < 1e-12 and abs(mid[1] + 1) < 1e-12 and (mid[2:] == 0).all()
+
+
+def test_nusselt_profile_closed_form(orc):
+    """A field the stencils take exactly: T = c(y) theta(x) with theta
+    quadratic in x (theta(0) = 1/2, theta(H) = -1/2, curvature alpha) and
+    c(y) = 1 + beta (y/H - 1/2), and a uniform velocity u_x = u0.  The plane
+    mean of c is 1 on any mesh, so every plane carries exactly
+    u0 theta(x_j) H/kappa - H theta'(x_j) (convection + conduction); the
+    mid-line through y = H/2 has c = 1 (one node line on the odd mesh, the
+    mean of the two bracketing lines on the even one), so Nu_mean is
+    -H theta'(0) = 1 - alpha at the hot wall and H theta'(H) = -(1 + alpha)
+    at the cold one.  A plane other than the middle, a dropped convective
+    term, a wrong sign or a first-order wall stencil each fail it."""
+    alpha, beta, u0 = 0.3, 0.4, 2e-3
+    for N in (9, 10):
+        H = float(N)
+        x = np.arange(N) + 0.5
+        y = np.arange(N) + 0.5
+        th = 0.5 - x / H + alpha * (x / H) * (1 - x / H)
+        dth = (-1 + alpha * (1 - 2 * x / H)) / H
+        c = 1 + beta * (y / H - 0.5)
+        T = c[None, :, None] * th[None, None, :] * np.ones((N, N, N))
+        # the Dirichlet walls carry the wall values of theta times c(y): use the
+        # mid-plane values 1/2 and -1/2; c(y) != 1 off the mid-plane makes the
+        # one-sided stencil there see another wall value, which must not leak
+        # into the mid-line or (by symmetry of c about the middle) the plane means
+        p = orc.Params(N, N, N, _walls([D, D, A, A, A, A], (0.5, -0.5, 0, 0, 0, 0)), 0.04, 0.03, 0.0, N, 0.1)
+        u = np.zeros((3, N, N, N))
+        u[0] = u0
+        f, g = orc.init_equilibrium(p, 1.0, u, T)
+        prof, mid = orc.nusselt_profile(p, f, g, axis=0)
+        want = u0 * th * H / p.kappa - H * dth
+        # wall layers: the one-sided stencil uses T_w = +-1/2 where the field
+        # has c(y) T_w; its plane mean is still exact because mean(c) = 1
+        assert np.abs(prof - want).max() < 1e-12, prof - want
+        assert abs(mid[0] - (1 - alpha)) < 1e-12 and abs(mid[1] + (1 + alpha)) < 1e-12
+        # along y (adiabatic walls, zero-gradient stencil next to them)
+        prof_y, _ = orc.nusselt_profile(p, f, g, axis=1)
+        dc = beta / H * th.mean()
+        want_y = -H * dc * np.ones(N)
+        want_y[0] = -H * 0.5 * (c[1] - c[0]) * th.mean()
+        want_y[-1] = -H * 0.5 * (c[-1] - c[-2]) * th.mean()
+        assert np.abs(prof_y - want_y).max() < 1e-12
+
+
 def test_local_dissipation_closed_forms(orc):
     """Per-node eps_u = nu/2 sum_ij (d_i u_j + d_j u_i)^2 and eps_T = kappa |grad T|^2
     (Sec. 4) on fields whose derivatives the stencils take exactly: u_x and the
