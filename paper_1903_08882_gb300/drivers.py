@@ -18,25 +18,41 @@ def free_fall_steps(H: float, U: float) -> float:
 
 
 def run_to_steady(lat, every: int = 1000, tol: float = 1e-7, max_steps: int = 2_000_000, face: int = 0,
-                  min_steps: int = 0):
+                  min_steps: int = 0, average: int = 1):
     """Advance until the relative change of the Nusselt number of Dirichlet
     face `face` over `every` steps is below `tol` (the steady criterion on the
     hot-wall Nusselt number; Sec. 3 uses a field criterion instead).
-    Returns dict(steps, converged, Nu, history, diag)."""
+    With average = k > 1 the criterion compares the means of the last k
+    samples and of the k before them (for storages whose stochastic rounding
+    leaves a small sample-to-sample noise on Nu), and Nu is the mean of the
+    last k samples.
+    Returns dict(steps, converged, Nu, history, diag, diag_mean): diag is the
+    last sample's diagnostics, diag_mean the wall Nusselt numbers (Nu_face,
+    Nu_link) averaged over the last k samples."""
+    k = max(1, int(average))
     lat.sample()
     prev = lat.diagnostics()["Nu_face"][face]
-    hist, steps = [prev], 0
+    hist, steps, walls = [prev], 0, []
+
+    def done(converged, d):
+        nu_face = np.mean([w[0] for w in walls[-k:]], axis=0)
+        nu_link = np.mean([w[1] for w in walls[-k:]], axis=0)
+        return dict(steps=steps, converged=converged, Nu=float(np.mean(hist[-k:])), history=np.array(hist),
+                    diag=d, diag_mean=dict(Nu_face=nu_face, Nu_link=nu_link))
+
     while steps < max_steps:
         lat.step(every)
         steps += every
         lat.sample()
         d = lat.diagnostics(reset=True)
-        nu = d["Nu_face"][face]
-        hist.append(nu)
-        if steps >= min_steps and abs(nu - prev) <= tol * abs(nu):
-            return dict(steps=steps, converged=True, Nu=nu, history=np.array(hist), diag=d)
-        prev = nu
-    return dict(steps=steps, converged=False, Nu=prev, history=np.array(hist), diag=d)
+        hist.append(d["Nu_face"][face])
+        walls.append((np.array(d["Nu_face"]), np.array(d.get("Nu_link", d["Nu_face"]))))
+        walls = walls[-k:]
+        if len(hist) > 2 * k and steps >= min_steps:
+            new, old = float(np.mean(hist[-k:])), float(np.mean(hist[-2 * k:-k]))
+            if abs(new - old) <= tol * abs(new):
+                return done(True, d)
+    return done(False, d)
 
 
 def grid_convergence(meshes, values):
@@ -206,16 +222,25 @@ def resolution(Ra: float, Pr: float, Nu: float, H: float):
     return dict(dg_over_eta=1.0 / eta, dg_over_etaB=1.0 / eta_B, tau_eta=tau_eta, N_BL=H / (2.0 * Nu))
 
 
+def _centre_pair(n: int):
+    """Node indices whose centres bracket the mid-point H/2 of an axis of n
+    nodes (node j at j + 1/2): one node for odd n, two for even n."""
+    return sorted({(n - 1) // 2, n // 2})
+
+
 def centerline_probes(u3, U: float):
     """Table 1 probes of the side-heated cell (hot wall at x = 0 here, so the
     paper's y is our x): maximum horizontal velocity u along the vertical
     centreline of the mid-plane y = 1/2, with its height z, and maximum
     vertical velocity w along the horizontal centreline, with its position x.
-    Velocities in free-fall units; positions at node centres (j + 1/2)/N."""
+    Velocities in free-fall units; positions at node centres (j + 1/2)/N.
+    On an even mesh the mid-plane falls between two node planes, and the
+    centreline values are interpolated linearly (the mean of the two, or of
+    the four lines around the centre)."""
     nz, ny, nx = u3.shape[1:]
-    jy, jx, jz = ny // 2, nx // 2, nz // 2
-    col = u3[0][:, jy, jx] / U
-    row = u3[2][jz, jy, :] / U
+    ys, xs, zs = _centre_pair(ny), _centre_pair(nx), _centre_pair(nz)
+    col = np.mean([u3[0][:, jy, jx] for jy in ys for jx in xs], axis=0) / U
+    row = np.mean([u3[2][jz, jy, :] for jz in zs for jy in ys], axis=0) / U
     k = int(np.argmax(np.abs(col)))
     i = int(np.argmax(np.abs(row)))
     return dict(u_max=float(col[k]), z=(k + 0.5) / nz, w_max=float(row[i]), x=(i + 0.5) / nx)

@@ -87,6 +87,25 @@ def test_centerline_probes_read_the_two_centrelines():
     assert p["w_max"] == pytest.approx(0.6) and p["x"] == pytest.approx(1.5 / 9)
 
 
+def test_centerline_probes_interpolate_on_even_meshes():
+    """On an even mesh (8 nodes: the mid-point lies between nodes 3 and 4) the
+    centreline of a field linear across it is the mean of the bracketing
+    lines, which equals the field's value at the exact centre."""
+    n, U = 8, 0.1
+    z, y, x = np.meshgrid(*(np.arange(n) + 0.5,) * 3, indexing="ij")
+    u3 = np.zeros((3, n, n, n))
+    prof = np.sin(np.pi * (z / n))  # u along z, peak at the centre of the column
+    u3[0] = U * prof * (1 + 0.3 * (x / n - 0.5) + 0.2 * (y / n - 0.5))
+    u3[2] = U * np.sin(2 * np.pi * (x / n)) * (1 - 0.4 * (y / n - 0.5) + 0.5 * (z / n - 0.5))
+    p = drivers.centerline_probes(u3, U)
+    want_col = np.sin(np.pi * (np.arange(n) + 0.5) / n)
+    want_row = np.sin(2 * np.pi * (np.arange(n) + 0.5) / n)
+    assert p["u_max"] == pytest.approx(want_col.max()) and p["z"] in ((3.5) / n, (4.5) / n)
+    assert abs(p["w_max"]) == pytest.approx(np.abs(want_row).max())
+    # the plain node lines ny // 2, nx // 2 would read 1 + 0.3/16 + 0.2/16 times the centre value
+    assert abs(p["u_max"] - want_col.max()) < 1e-12
+
+
 def _stretched_norm(alpha, m):
     """C that normalises C X^-1/2 exp(-m X^alpha) on X > 0: with Y = m X^alpha,
     Y follows a Gamma distribution of shape 1/(2 alpha)."""
@@ -279,3 +298,55 @@ def test_warm_start_summary_statistics():
     assert n["geomean"] == pytest.approx(np.sqrt(8.0)) and n["median"] == 3.0 and n["mean"] == 3.75
     assert n["frac_ge_3"] == 0.5 and n["n"] == 4
     assert out["speedup_judged"]["geomean"] == 1.0 and "speedup_coarse" not in out
+
+
+class _RelaxingNu:
+    """Stands in for a Lattice: Nu relaxes exponentially towards nu_inf (e-fold
+    over `tau` steps) plus a seeded noise of relative size `noise` per sample."""
+
+    def __init__(self, nu_inf=8.8, amp=0.5, tau=20_000.0, noise=0.0, seed=3):
+        self.t, self.nu_inf, self.amp, self.tau, self.noise = 0, nu_inf, amp, tau, noise
+        self.rng = np.random.default_rng(seed)
+
+    def step(self, n):
+        self.t += n
+
+    def sample(self):
+        pass
+
+    def diagnostics(self, reset=False):
+        nu = self.nu_inf + self.amp * np.exp(-self.t / self.tau)
+        nu *= 1.0 + self.noise * self.rng.standard_normal()
+        return {"Nu_face": np.array([nu, -nu, 0, 0, 0, 0])}
+
+
+def test_run_to_steady_plain_criterion():
+    """average = 1: stops at the first 1000-step change below tol; the change
+    of an exponential over the 1000 steps before t is amp e^(-t/tau) (e^(1000/tau) - 1)."""
+    from paper_1903_08882_gb300 import drivers
+
+    lat = _RelaxingNu()
+    r = drivers.run_to_steady(lat, every=1000, tol=1e-7, max_steps=10**6)
+    assert r["converged"]
+    t = r["steps"]
+    change = lambda t: 0.5 * np.exp(-t / 2e4) * np.expm1(1000 / 2e4)
+    nu = lambda t: 8.8 + 0.5 * np.exp(-t / 2e4)
+    assert change(t) <= 1e-7 * nu(t) and change(t - 1000) > 1e-7 * nu(t - 1000)
+    assert abs(r["Nu"] - 8.8) < 2e-5  # stops amp e^(-t/tau) ~ 1.7e-5 short of the limit
+
+
+def test_run_to_steady_averaged_criterion_with_noise():
+    """A noise of 5e-5 per sample (the stochastic rounding's scale at 65^3)
+    never meets the plain 1e-7 rule; means of 20 samples (noise 1.6e-5 on
+    their difference) meet a 3e-5 rule only once the exponential's change
+    over 20 samples has fallen to that scale, leaving Nu within 1e-4."""
+    from paper_1903_08882_gb300 import drivers
+
+    lat = _RelaxingNu(noise=5e-5)
+    r = drivers.run_to_steady(lat, every=1000, tol=1e-7, max_steps=400_000)
+    assert not r["converged"]
+    lat = _RelaxingNu(noise=5e-5)
+    r = drivers.run_to_steady(lat, every=1000, tol=3e-5, max_steps=2_000_000, average=20)
+    assert r["converged"]
+    assert abs(r["Nu"] - 8.8) / 8.8 < 1e-4
+    assert 0.5 * np.exp(-r["steps"] / 2e4) < 1e-4 * 8.8
