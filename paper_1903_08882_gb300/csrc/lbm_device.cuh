@@ -63,21 +63,77 @@ enum StorageKind { ST_F32 = 0, ST_F16 = 1, ST_BF16 = 2, ST_F16M = 3 };
 __host__ __device__ constexpr int FS(int S) { return S == ST_F16M ? ST_F16 : S; }
 __host__ __device__ constexpr int GS(int S) { return S == ST_F16M ? ST_F32 : S; }
 
+// ------------------------------------------------- stochastic rounding ----
+//
+// The 2-byte storages round the thermal populations stochastically: a value
+// is stored as one of the two neighbouring 2-byte numbers, the one above with
+// probability equal to the fraction of the gap it covers, so the stored value
+// is unbiased.  Rounding to nearest loses every update smaller than half the
+// spacing, which freezes the slow approach to a steady state far from it: the
+// rest population g_0 = (1 - a_T)/7 T holds 60-97% of T ~ 1/2 to ~2e-4 while
+// a step changes T by ~1e-6, and the rounding of the moving ones biases the
+// wall heat flux they carry by ~0.5% on a 33^3 cell.  Unbiased rounding keeps
+// those updates on average.  The random bits are a counter-based hash of
+// (node, time step) spread over the populations, so runs are reproducible
+// and every kernel variant draws the same bits for a value.
+__host__ __device__ constexpr bool SRG(int S) { return S == ST_F16 || S == ST_BF16; }
+
+// 32 random bits of node n at time step t (multiply-xorshift hash).
+__host__ __device__ __forceinline__ uint32_t rnd_node(uint32_t n, uint32_t t) {
+    uint32_t x = (n ^ (t * 0x9E3779B9u)) * 0x85EBCA6Bu;
+    x ^= x >> 13;
+    return x * 0xC2B2AE35u;
+}
+// Bits for population q of that node: the node's bits times an odd constant
+// per population (the high bits are used).
+__host__ __device__ __forceinline__ uint32_t rnd_pop(uint32_t r, int q) {
+    return r * (0x9E3779B1u + 0x3C6EF372u * static_cast<uint32_t>(q));
+}
+// Stochastic rounding of an FP32 value to FP16 / BF16: add random bits below
+// the kept significand to the magnitude, then truncate towards zero (exact
+// for normal numbers; below the FP16 normal range, 6.1e-5, the result can be
+// biased towards zero by less than one FP16 subnormal spacing, 6e-8).
+__device__ __forceinline__ float sr_pre16(float v, uint32_t r) {
+    return __uint_as_float(__float_as_uint(v) + (r >> 19));
+}
+__device__ __forceinline__ float sr_pre_bf(float v, uint32_t r) {
+    return __uint_as_float(__float_as_uint(v) + (r >> 16));
+}
+__device__ __forceinline__ __half2 h2_sr(float2 v, uint32_t r0, uint32_t r1) {
+    uint32_t o;
+    asm("cvt.rz.f16x2.f32 %0, %1, %2;" : "=r"(o) : "f"(sr_pre16(v.y, r1)), "f"(sr_pre16(v.x, r0)));
+    return *reinterpret_cast<__half2 *>(&o);
+}
+__device__ __forceinline__ __nv_bfloat162 bf2_sr(float2 v, uint32_t r0, uint32_t r1) {
+    uint32_t o;
+    asm("cvt.rz.bf16x2.f32 %0, %1, %2;" : "=r"(o) : "f"(sr_pre_bf(v.y, r1)), "f"(sr_pre_bf(v.x, r0)));
+    return *reinterpret_cast<__nv_bfloat162 *>(&o);
+}
+
 template <int S> struct Store;
+// st: round to nearest; sts: the thermal populations' rounding, given 32
+// random bits r (stochastic for the 2-byte formats, see SRG above).
 template <> struct Store<ST_F32> {
     using T = float;
     static __device__ __forceinline__ float ld(const float *p) { return *p; }
     static __device__ __forceinline__ void st(float *p, float v) { *p = v; }
+    static __device__ __forceinline__ void sts(float *p, float v, uint32_t) { *p = v; }
 };
 template <> struct Store<ST_F16> {
     using T = __half;
     static __device__ __forceinline__ float ld(const __half *p) { return __half2float(*p); }
     static __device__ __forceinline__ void st(__half *p, float v) { *p = __float2half_rn(v); }
+    static __device__ __forceinline__ void sts(__half *p, float v, uint32_t r) {
+        *p = __float2half_rz(sr_pre16(v, r));
+    }
 };
 template <> struct Store<ST_BF16> {
     using T = __nv_bfloat16;
     static __device__ __forceinline__ float ld(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
     static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+    static __device__ __forceinline__ void sts(__nv_bfloat16 *p, float v, uint32_t r) {
+        *p = __float2bfloat16_rz(sr_pre_bf(v, r));
+    }
 };
 
 // Two consecutive elements (first index even, so 4- or 8-byte aligned).
@@ -85,6 +141,7 @@ template <int S> struct Store2;
 template <> struct Store2<ST_F32> {
     static __device__ __forceinline__ float2 ld(const float *p) { return *reinterpret_cast<const float2 *>(p); }
     static __device__ __forceinline__ void st(float *p, float2 v) { *reinterpret_cast<float2 *>(p) = v; }
+    static __device__ __forceinline__ void sts(float *p, float2 v, uint32_t, uint32_t) { st(p, v); }
 };
 template <> struct Store2<ST_F16> {
     static __device__ __forceinline__ float2 ld(const __half *p) {
@@ -93,6 +150,9 @@ template <> struct Store2<ST_F16> {
     static __device__ __forceinline__ void st(__half *p, float2 v) {
         *reinterpret_cast<__half2 *>(p) = __float22half2_rn(v);
     }
+    static __device__ __forceinline__ void sts(__half *p, float2 v, uint32_t r0, uint32_t r1) {
+        *reinterpret_cast<__half2 *>(p) = h2_sr(v, r0, r1);
+    }
 };
 template <> struct Store2<ST_BF16> {
     static __device__ __forceinline__ float2 ld(const __nv_bfloat16 *p) {
@@ -100,6 +160,9 @@ template <> struct Store2<ST_BF16> {
     }
     static __device__ __forceinline__ void st(__nv_bfloat16 *p, float2 v) {
         *reinterpret_cast<__nv_bfloat162 *>(p) = __float22bfloat162_rn(v);
+    }
+    static __device__ __forceinline__ void sts(__nv_bfloat16 *p, float2 v, uint32_t r0, uint32_t r1) {
+        *reinterpret_cast<__nv_bfloat162 *>(p) = bf2_sr(v, r0, r1);
     }
 };
 
@@ -132,6 +195,7 @@ struct Phys {
     float bf[3];     // constant body-force density
     float abbT[6];   // (6 + a_T)/21 T_w of each Dirichlet face
     int dir_mask;    // bit f: face f is a Dirichlet wall
+    uint32_t t;      // time step being taken (low 32 bits): the stochastic rounding's counter
 };
 
 // a / d for 32-bit a and d, given mag = ceil(2^64 / d) (exact: the rounding
@@ -537,14 +601,16 @@ __device__ __forceinline__ void odd_step_node(SEF<S> *__restrict__ f, SEG<S> *__
         else
             Store<FS(S)>::st(f + opp19(i) * s + n, fl[i]);
     }
+    const uint32_t rb = SRG(S) ? rnd_node(n, P.t) : 0u;
+    Store<GS(S)>::sts(g + n, gl[0], rnd_pop(rb, 0));
 #pragma unroll
-    for (int i = 0; i < 7; ++i) {
+    for (int i = 1; i < 7; ++i) {
         if (!dst_wall(b, ex7(i), ey7(i), ez7(i))) {
-            Store<GS(S)>::st(g + i * s + (int64_t)n + dst_off(b, ex7(i), ey7(i), ez7(i)), gl[i]);
+            Store<GS(S)>::sts(g + i * s + (int64_t)n + dst_off(b, ex7(i), ey7(i), ez7(i)), gl[i], rnd_pop(rb, i));
         } else {
             const int fc = face_of(ex7(i), ey7(i), ez7(i));
             const float v = gl[i];
-            Store<GS(S)>::st(g + opp7(i) * s + n, ((P.dir_mask >> fc) & 1) ? P.abbT[fc] - v : v);
+            Store<GS(S)>::sts(g + opp7(i) * s + n, ((P.dir_mask >> fc) & 1) ? P.abbT[fc] - v : v, rnd_pop(rb, i));
         }
     }
     if (MOM) write_sample(mom, s, n, m, b, g0);

@@ -84,8 +84,10 @@ __global__ void __launch_bounds__(256, 3) k_aa_even(SEF<S> *__restrict__ f, SEG<
     g = opaque(g);
 #pragma unroll
     for (int i = 0; i < 19; ++i) Store<FS(S)>::st(f + opp19(i) * s + n, fl[i]);
+    const uint32_t rb = SRG(S) ? rnd_node(n, P.t) : 0u;
 #pragma unroll
-    for (int i = 0; i < 7; ++i) Store<GS(S)>::st(g + opp7(i) * s + n, gl[i]);
+#pragma unroll
+    for (int i = 0; i < 7; ++i) Store<GS(S)>::sts(g + opp7(i) * s + n, gl[i], rnd_pop(rb, i));
     if (MOM) {
         int x, y, z;
         node_xyz(G, n, x, y, z);
@@ -124,9 +126,10 @@ __global__ void __launch_bounds__(256, 3) k_aa_odd_interior(SEF<S> *__restrict__
     Store<FS(S)>::st(f + n, fl[0]);
 #pragma unroll
     for (int i = 1; i < 19; ++i) Store<FS(S)>::st(f + i * s + (int64_t)(n + G.off[i]), fl[i]);
-    Store<GS(S)>::st(g + n, gl[0]);
+    const uint32_t rb = SRG(S) ? rnd_node(n, P.t) : 0u;
+    Store<GS(S)>::sts(g + n, gl[0], rnd_pop(rb, 0));
 #pragma unroll
-    for (int i = 1; i < 7; ++i) Store<GS(S)>::st(g + i * s + (int64_t)(n + G.off[i]), gl[i]);
+    for (int i = 1; i < 7; ++i) Store<GS(S)>::sts(g + i * s + (int64_t)(n + G.off[i]), gl[i], rnd_pop(rb, i));
     if (MOM) {
         mom[n] = m.drho;
         mom[s + n] = m.u;
@@ -180,8 +183,10 @@ __device__ __forceinline__ void k_aa_even2_tile(SEF<S> *__restrict__ f, SEG<S> *
     g = opaque(g);
 #pragma unroll
     for (int i = 0; i < 19; ++i) Store2<FS(S)>::st(f + opp19(i) * s + n, fl[i]);
+    const uint32_t rb0 = SRG(S) ? rnd_node(n, P.t) : 0u, rb1 = SRG(S) ? rnd_node(n + 1u, P.t) : 0u;
 #pragma unroll
-    for (int i = 0; i < 7; ++i) Store2<GS(S)>::st(g + opp7(i) * s + n, gl[i]);
+#pragma unroll
+    for (int i = 0; i < 7; ++i) Store2<GS(S)>::sts(g + opp7(i) * s + n, gl[i], rnd_pop(rb0, i), rnd_pop(rb1, i));
     if (MOM) {
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
@@ -302,14 +307,15 @@ __device__ __forceinline__ void k_aa_odd_rows_tile(SEF<S> *__restrict__ f, SEG<S
             if (a1) Store<FS(S)>::st(w1 ? own + 32 : q + 32, fl[i].y);
         }
     }
-    if (a0) Store<GS(S)>::st(g + n0, gl[0].x);
-    if (a1) Store<GS(S)>::st(g + n0 + 32, gl[0].y);
+    const uint32_t rb0 = SRG(S) ? rnd_node(n0, P.t) : 0u, rb1 = SRG(S) ? rnd_node(n0 + 32u, P.t) : 0u;
+    if (a0) Store<GS(S)>::sts(g + n0, gl[0].x, rnd_pop(rb0, 0));
+    if (a1) Store<GS(S)>::sts(g + n0 + 32, gl[0].y, rnd_pop(rb1, 0));
 #pragma unroll
     for (int i = 1; i < 7; ++i) {
         SEG<S> *q = g + i * s + (int64_t)(n0 + G.off[i]);
         if (ex7(i) == 0) {
-            if (a0) Store<GS(S)>::st(q, gl[i].x);
-            if (a1) Store<GS(S)>::st(q + 32, gl[i].y);
+            if (a0) Store<GS(S)>::sts(q, gl[i].x, rnd_pop(rb0, i));
+            if (a1) Store<GS(S)>::sts(q + 32, gl[i].y, rnd_pop(rb1, i));
         } else {
             const bool w0 = ex7(i) > 0 ? hi0 : lo0, w1 = ex7(i) > 0 ? hi1 : lo1;
             SEG<S> *own = per ? q - (ex7(i) > 0 ? (int64_t)nx : -(int64_t)nx) : g + opp7(i) * s + n0;
@@ -319,8 +325,8 @@ __device__ __forceinline__ void k_aa_odd_rows_tile(SEF<S> *__restrict__ f, SEG<S
                 if (w0) v.x = P.abbT[fc] - v.x;
                 if (w1) v.y = P.abbT[fc] - v.y;
             }
-            if (a0) Store<GS(S)>::st(w0 ? own : q, v.x);
-            if (a1) Store<GS(S)>::st(w1 ? own + 32 : q + 32, v.y);
+            if (a0) Store<GS(S)>::sts(w0 ? own : q, v.x, rnd_pop(rb0, i));
+            if (a1) Store<GS(S)>::sts(w1 ? own + 32 : q + 32, v.y, rnd_pop(rb1, i));
         }
     }
     if (MOM) {
@@ -370,6 +376,9 @@ __global__ void __launch_bounds__(BS, BS == 128 ? 3 : 2)
     // fields are re-read cheaply instead of held in registers
     __shared__ CellDev sc;
     __shared__ Tile st;
+    // steps the batch took before this launch: every block reads it before the
+    // first grid barrier, block 0 advances it after the last one
+    const uint32_t t0 = *reinterpret_cast<volatile unsigned *>(&bar->steps);
     for (int step = 0; step < nsteps; ++step) {
         const bool odd_step = ((parity0 + step) & 1) != 0;
         const Tile *tl = odd_step ? odd : even;
@@ -379,6 +388,7 @@ __global__ void __launch_bounds__(BS, BS == 128 ? 3 : 2)
             if (threadIdx.x == 0) {
                 st = tl[t];
                 sc = cells[st.cell];
+                sc.P.t += t0 + (uint32_t)step; // the cell's time step (stochastic rounding counter)
             }
             __syncthreads();
             SEF<S> *f = static_cast<SEF<S> *>(sc.f);
@@ -392,6 +402,7 @@ __global__ void __launch_bounds__(BS, BS == 128 ? 3 : 2)
         }
         if (!grid_barrier(bar, gridDim.x, budget)) return;
     }
+    if (blockIdx.x == 0 && threadIdx.x == 0) bar->steps = t0 + (uint32_t)nsteps;
 }
 
 template <int S> static const void *batch_kernel(int block) {
@@ -442,8 +453,10 @@ __global__ void __launch_bounds__(256, 3) k_pull(const SEF<S> *__restrict__ fs, 
     const int64_t s = G.stride;
 #pragma unroll
     for (int i = 0; i < 19; ++i) Store<FS(S)>::st(fd + i * s + n, fl[i]);
+    const uint32_t rb = SRG(S) ? rnd_node(n, P.t) : 0u;
 #pragma unroll
-    for (int i = 0; i < 7; ++i) Store<GS(S)>::st(gd + i * s + n, gl[i]);
+#pragma unroll
+    for (int i = 0; i < 7; ++i) Store<GS(S)>::sts(gd + i * s + n, gl[i], rnd_pop(rb, i));
     if (MOM) write_sample(mom, s, n, m, neighbours(G, x, y, z), g0);
 }
 
@@ -562,6 +575,32 @@ __global__ void k_equilibrium(float *__restrict__ st, const float *__restrict__ 
     }
 }
 
+// Equilibrium state of host-order FP64 fields (rho, u3[3][n], T, as given to
+// lbm_set_fields and copied to the device), stored straight into the natural
+// device layout (the AA pattern before an even step): the deviations of
+// k_equilibrium, rounded to the storage format once.
+template <int S>
+__global__ void k_fields_natural(const double *__restrict__ rho, const double *__restrict__ u3,
+                                 const double *__restrict__ Tf, SEF<S> *__restrict__ f, SEG<S> *__restrict__ g,
+                                 uint32_t N, int64_t s, Phys P) {
+    const uint32_t n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const float dr = (float)(rho[n] - 1.0), u = (float)u3[n], v = (float)u3[(int64_t)N + n];
+    const float w = (float)u3[2 * (int64_t)N + n], T = (float)Tf[n];
+    const float r = 1.f + dr, uu = u * u + v * v + w * w;
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        const float eu = ex19(i) * u + ey19(i) * v + ez19(i) * w;
+        Store<FS(S)>::st(f + i * s + n, w19(i) * (dr + r * (3.f * eu + 4.5f * eu * eu - 1.5f * uu)));
+    }
+    const float w0 = (1.f - P.a_T) / 7.f, w1 = (6.f + P.a_T) / 42.f, c = 21.f / (6.f + P.a_T);
+#pragma unroll
+    for (int i = 0; i < 7; ++i) {
+        const float eu = ex7(i) * u + ey7(i) * v + ez7(i) * w;
+        Store<GS(S)>::st(g + i * s + n, (i == 0 ? w0 : w1) * T * (1.f + c * eu));
+    }
+}
+
 // ---------------------------------------------------------- launchers ----
 
 static inline unsigned blocks_for(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
@@ -673,6 +712,24 @@ cudaError_t launch_gather(int storage, float *out, const int64_t *nodes, int64_t
     case ST_F16: return gather_t<ST_F16>(out, nodes, count, f, g, G, P, layout, stream);
     case ST_F16M: return gather_t<ST_F16M>(out, nodes, count, f, g, G, P, layout, stream);
     default: return gather_t<ST_BF16>(out, nodes, count, f, g, G, P, layout, stream);
+    }
+}
+
+template <int S>
+static cudaError_t fields_t(const double *rho, const double *u3, const double *T, void *f, void *g, const Geom &G,
+                            const Phys &P, cudaStream_t stream) {
+    k_fields_natural<S><<<blocks_for(G.n, 256), 256, 0, stream>>>(rho, u3, T, (SEF<S> *)f, (SEG<S> *)g, G.n,
+                                                                   G.stride, P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fields_natural(int storage, const double *rho, const double *u3, const double *T, void *f,
+                                  void *g, const Geom &G, const Phys &P, cudaStream_t stream) {
+    switch (storage) {
+    case ST_F32: return fields_t<ST_F32>(rho, u3, T, f, g, G, P, stream);
+    case ST_F16: return fields_t<ST_F16>(rho, u3, T, f, g, G, P, stream);
+    case ST_F16M: return fields_t<ST_F16M>(rho, u3, T, f, g, G, P, stream);
+    default: return fields_t<ST_BF16>(rho, u3, T, f, g, G, P, stream);
     }
 }
 

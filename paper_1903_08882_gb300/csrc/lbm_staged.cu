@@ -113,10 +113,15 @@ __device__ __forceinline__ float tof(__half v) { return __half2float(v); }
 __device__ __forceinline__ float tof(__nv_bfloat16 v) { return __bfloat162float(v); }
 
 template <typename E> struct Pair;
+// st / st1: round to nearest; sts / st1s: stochastic rounding with the
+// random bits r (the thermal populations of the 2-byte storages, see
+// lbm_device.cuh).
 template <> struct Pair<float> {
     static __device__ __forceinline__ float2 ld(const float *p) { return *reinterpret_cast<const float2 *>(p); }
     static __device__ __forceinline__ void st(float *p, float2 v) { *reinterpret_cast<float2 *>(p) = v; }
     static __device__ __forceinline__ void st1(float *p, float v) { *p = v; }
+    static __device__ __forceinline__ void sts(float *p, float2 v, uint32_t, uint32_t) { st(p, v); }
+    static __device__ __forceinline__ void st1s(float *p, float v, uint32_t) { *p = v; }
 };
 template <> struct Pair<__half> {
     static __device__ __forceinline__ float2 ld(const __half *p) {
@@ -126,6 +131,10 @@ template <> struct Pair<__half> {
         *reinterpret_cast<__half2 *>(p) = __float22half2_rn(v);
     }
     static __device__ __forceinline__ void st1(__half *p, float v) { *p = __float2half_rn(v); }
+    static __device__ __forceinline__ void sts(__half *p, float2 v, uint32_t r0, uint32_t r1) {
+        *reinterpret_cast<__half2 *>(p) = h2_sr(v, r0, r1);
+    }
+    static __device__ __forceinline__ void st1s(__half *p, float v, uint32_t r) { *p = __float2half_rz(sr_pre16(v, r)); }
 };
 template <> struct Pair<__nv_bfloat16> {
     static __device__ __forceinline__ float2 ld(const __nv_bfloat16 *p) {
@@ -135,6 +144,12 @@ template <> struct Pair<__nv_bfloat16> {
         *reinterpret_cast<__nv_bfloat162 *>(p) = __float22bfloat162_rn(v);
     }
     static __device__ __forceinline__ void st1(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+    static __device__ __forceinline__ void sts(__nv_bfloat16 *p, float2 v, uint32_t r0, uint32_t r1) {
+        *reinterpret_cast<__nv_bfloat162 *>(p) = bf2_sr(v, r0, r1);
+    }
+    static __device__ __forceinline__ void st1s(__nv_bfloat16 *p, float v, uint32_t r) {
+        *p = __float2bfloat16_rz(sr_pre_bf(v, r));
+    }
 };
 
 // Flat offset of e_i for population q (0..18 flow, 19..25 thermal: the D3Q7
@@ -282,8 +297,10 @@ __global__ void __launch_bounds__(kThreads, 2)
                 if (v0) {
 #pragma unroll
                     for (int q = 0; q < 19; ++q) Pair<SF<S>>::st(fo + opp19(q) * s + m, fl[q]);
+                    const uint32_t rb0 = SRG(S) ? rnd_node(m, P.t) : 0u, rb1 = SRG(S) ? rnd_node(mb, P.t) : 0u;
 #pragma unroll
-                    for (int q = 0; q < 7; ++q) Pair<SG<S>>::st(go + opp7(q) * s + m, gl[q]);
+                    for (int q = 0; q < 7; ++q)
+                        Pair<SG<S>>::sts(go + opp7(q) * s + m, gl[q], rnd_pop(rb0, q), rnd_pop(rb1, q));
                 }
             } else {
 #pragma unroll
@@ -292,11 +309,12 @@ __global__ void __launch_bounds__(kThreads, 2)
                     if (v0) Pair<SF<S>>::st1(p, fl[q].x);
                     if (v1) Pair<SF<S>>::st1(p + 32, fl[q].y);
                 }
+                const uint32_t rb0 = SRG(S) ? rnd_node(m, P.t) : 0u, rb1 = SRG(S) ? rnd_node(mb, P.t) : 0u;
 #pragma unroll
                 for (int q = 0; q < 7; ++q) {
                     SG<S> *p = go + q * s + (int64_t)m + G.off[q];
-                    if (v0) Pair<SG<S>>::st1(p, gl[q].x);
-                    if (v1) Pair<SG<S>>::st1(p + 32, gl[q].y);
+                    if (v0) Pair<SG<S>>::st1s(p, gl[q].x, rnd_pop(rb0, q));
+                    if (v1) Pair<SG<S>>::st1s(p + 32, gl[q].y, rnd_pop(rb1, q));
                 }
             }
         }
