@@ -218,6 +218,26 @@ lbm_status lbm_moments(lbm_ctx *ctx, double *rho, double *u3, double *T);
 lbm_status lbm_dissipation_pdf(lbm_ctx *ctx, int nbins, double xmax, const double *rms_in, double *rms_out,
                                uint64_t *counts_u, uint64_t *counts_T);
 
+/* Nusselt numbers of Sec. 3 beyond the wall averages, of the current state,
+ * with the temperature difference of the walls taken as 1 and lengths in
+ * units of H (lbm_constants.H):
+ *   profile[n_axis] (host, overwritten): the plane-averaged Nusselt number
+ *     along `axis` (0 = x, 1 = y, 2 = z), the x-z plane average Nu(y) of the
+ *     paper's Fig. 4 taken along any axis: for every node plane j,
+ *     the mean over the plane's nodes of u_a T H / kappa - H dT/dx_a
+ *     (the paper's v T sqrt(Ra Pr) - dT/dy in lattice units), dT/dx_a with
+ *     the derivative stencils of the diagnostics;
+ *   nu_mid[6] (host, optional): for each face -x, +x, -y, +y, -z, +z, the
+ *     mid-line Nusselt number Nu_mean of Table 2: the mean of -H dT/dn at the
+ *     wall (n into the fluid, the stencil of lbm_diag.Nu_face) over the nodes
+ *     next to the face on the line along z (along x for the z faces) through
+ *     the middle of the third axis; for an even node count along that axis
+ *     the mean over the two node lines that bracket its middle; 0 for a face
+ *     that is not a Dirichlet wall.
+ * Synchronises the stream.  Errors: LBM_ERR_PARAM (axis outside 0..2, NULL
+ * profile), LBM_ERR_OOM (device scratch), LBM_ERR_CUDA, LBM_ERR_TIMEOUT. */
+lbm_status lbm_nusselt_profile(lbm_ctx *ctx, int axis, double *profile, double *nu_mid);
+
 /* Sample the diagnostics of the current state now (adds to the averages). */
 lbm_status lbm_sample(lbm_ctx *ctx);
 
@@ -313,7 +333,8 @@ lbm_status lbm_batch_set_barrier_budget(lbm_batch *batch, int64_t cycles);
  * already holds on the device, and allocates nothing: its per-block partial
  * sums live in a fixed static device array of LBM_NOALLOC_MAX_BLOCKS rows of
  * LBM_NDIAG doubles plus LBM_NDIAG + 1 accumulator slots (233,672 bytes),
- * which every GPU that loads the library holds until the process exits.
+ * which every GPU on which the library's code is loaded holds until the
+ * process exits.
  *
  *   fields  device, 11 arrays of `stride` floats, x fastest: rho - rho0, u, v,
  *           w, T of every node, then for each face f = 0..5 the pre-collision
@@ -327,13 +348,18 @@ lbm_status lbm_batch_set_barrier_budget(lbm_batch *batch, int64_t cycles);
  *           LBM_ERR_PARAM.
  *   sums    device, LBM_NDIAG doubles receiving the raw sums (lbm_diag.raw).
  *   stream  cudaStream_t the kernels run on (NULL: legacy default stream).
- * Asynchronous.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) and caches it; make that first call before
- * any stream capture.  All calls share the array and it keeps the last
- * call's contents: the accumulator slots are cleared at the start of every
- * call, and calls that overlap on a GPU race.  Errors: LBM_ERR_PARAM for an
- * invalid argument, LBM_ERR_CUDA for a failed launch; lbm_last_error(NULL)
- * describes it. */
+ * Asynchronous.  When the array's memory is taken: CUDA loads device code
+ * per context, lazily by default, and the array is allocated when the code
+ * holding it is loaded, which happens at the array's address look-up
+ * (cudaGetSymbolAddress).  lbm_create does that look-up for its device, so
+ * after creating a context on a device the array is held and no later call
+ * allocates.  Without a context, the first call on a device does it: make
+ * that first call during set-up, before any stream capture.  The address is
+ * cached per CUDA context and looked up again if the device was reset.  All
+ * calls share the array and it keeps the last call's contents: the
+ * accumulator slots are cleared at the start of every call, and calls that
+ * overlap on a GPU race.  Errors: LBM_ERR_PARAM for an invalid argument,
+ * LBM_ERR_CUDA for a failed launch; lbm_last_error(NULL) describes it. */
 #define LBM_NOALLOC_MAX_BLOCKS 1216
 lbm_status lbm_reduce_noalloc(const float *fields, int64_t stride, int nx, int ny, int nz,
                               const lbm_wall *walls, double a_T, int blocks, double *sums, void *stream);

@@ -338,6 +338,11 @@ lbm_status lbm_create(const lbm_params *params, const lbm_allocator *alloc, void
         delete ctx;
         return fail(nullptr, LBM_ERR_CUDA, "no CUDA device");
     }
+    // take the static scratch of lbm_reduce_noalloc on this device now, at set-up
+    if (noalloc_setup() != cudaSuccess) {
+        delete ctx;
+        return fail(nullptr, LBM_ERR_CUDA, "cannot load the library's device code on this device");
+    }
     ctx->block = params->block_size ? params->block_size : 128;
     ctx->elem = params->storage == LBM_FP32 ? 4 : 2;
     ctx->elem_g = (params->storage == LBM_FP32 || params->storage == LBM_FP16M) ? 4 : 2;
@@ -513,6 +518,22 @@ lbm_status lbm_set_fields(lbm_ctx *ctx, const double *rho, const double *u3, con
     if (!ctx || !rho || !u3 || !T) return ctx ? fail(ctx, LBM_ERR_PARAM, "NULL array") : LBM_ERR_PARAM;
     DeviceGuard dg(ctx->dev);
     const size_t n = (size_t)ctx->c.nodes;
+    if (ctx->p.streaming == LBM_STREAM_AA) {
+        // the fields go to the device as they are (FP64) into the sample
+        // arrays, which the next sample rewrites anyway (5 doubles fit in
+        // their 11 floats per node), and one kernel writes the equilibrium
+        // state into the natural layout: no allocation, no host conversion
+        static_assert(kMomArrays * sizeof(float) >= 5 * sizeof(double), "sample arrays too small for the fields");
+        double *d = reinterpret_cast<double *>(ctx->mom);
+        CK(ctx, cudaMemcpyAsync(d, rho, n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+        CK(ctx, cudaMemcpyAsync(d + n, u3, 3 * n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+        CK(ctx, cudaMemcpyAsync(d + 4 * n, T, n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+        CK(ctx, launch_fields_natural(ctx->p.storage, d, d + n, d + 4 * n, ctx->fbase(0), ctx->gbase(0), ctx->G,
+                                      ctx->P, ctx->stream));
+        ctx->parity = 0;
+        CK(ctx, cudaStreamSynchronize(ctx->stream));
+        return LBM_OK;
+    }
     float *fields = ctx->host_stage(5 * n * sizeof(float));
     if (!fields) return fail(ctx, LBM_ERR_OOM, "pinned host staging allocation failed");
     CK(ctx, cudaStreamSynchronize(ctx->stream));
@@ -528,10 +549,9 @@ lbm_status lbm_set_fields(lbm_ctx *ctx, const double *rho, const double *u3, con
     if (!fd.ptr || !st.ptr) return fail(ctx, LBM_ERR_OOM, "staging allocation failed");
     CK(ctx, cudaMemcpyAsync(fd.ptr, fields, 5 * n * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
     CK(ctx, launch_equilibrium((float *)st.ptr, (const float *)fd.ptr, (uint32_t)n, ctx->P, ctx->stream));
-    if (ctx->p.streaming == LBM_STREAM_AA) ctx->parity = 0;
-    const int layout = ctx->p.streaming == LBM_STREAM_PULL2 ? 2 : 0;
-    CK(ctx, launch_convert(ctx->p.storage, 0, (float *)st.ptr, ctx->fbase(0), ctx->gbase(0), ctx->G,
-                           ctx->P, layout, ctx->stream));
+    // the pull layout stores wall links as reflected values (layout conversion)
+    CK(ctx, launch_convert(ctx->p.storage, 0, (float *)st.ptr, ctx->fbase(0), ctx->gbase(0), ctx->G, ctx->P, 2,
+                           ctx->stream));
     CK(ctx, cudaStreamSynchronize(ctx->stream));
     return LBM_OK;
 }
@@ -609,6 +629,7 @@ lbm_status lbm_step(lbm_ctx *ctx, int64_t nsteps) {
         const bool sample = ctx->p.diag_every > 0 && ctx->step % ctx->p.diag_every == 0;
         a.mom = sample ? ctx->mom : nullptr;
         a.parity = ctx->parity;
+        a.P.t = (uint32_t)ctx->step;
         a.f = ctx->fbase(0);
         a.g = ctx->gbase(0);
         a.f2 = ctx->fbase(1);
@@ -695,6 +716,33 @@ lbm_status lbm_dissipation_pdf(lbm_ctx *ctx, int nbins, double xmax, const doubl
         rms_out[0] = rms[0];
         rms_out[1] = rms[1];
     }
+    return LBM_OK;
+}
+
+lbm_status lbm_nusselt_profile(lbm_ctx *ctx, int axis, double *profile, double *nu_mid) {
+    if (!ctx) return LBM_ERR_PARAM;
+    if (axis < 0 || axis > 2) return fail(ctx, LBM_ERR_PARAM, "axis must be 0, 1 or 2");
+    if (!profile) return fail(ctx, LBM_ERR_PARAM, "NULL profile array");
+    DeviceGuard dg(ctx->dev);
+    const int na = axis == 0 ? ctx->G.nx : axis == 1 ? ctx->G.ny : ctx->G.nz;
+    // moments of the current state into the sample arrays, as lbm_moments does
+    CK(ctx, launch_convert(ctx->p.storage, 2, ctx->mom, ctx->fbase(0), ctx->gbase(0), ctx->G, ctx->P,
+                           ctx->layout(), ctx->stream));
+    const size_t bytes = ((size_t)na + 6) * sizeof(double);
+    Scratch sc(ctx, bytes);
+    if (!sc.ptr) return fail(ctx, LBM_ERR_OOM, "staging allocation failed");
+    double *dev = static_cast<double *>(sc.ptr);
+    CK(ctx, cudaMemsetAsync(sc.ptr, 0, bytes, ctx->stream));
+    CK(ctx, launch_nu_profile(ctx->mom, ctx->G, ctx->P, ctx->wallT, axis, (float)ctx->c.H, (float)ctx->c.kappa,
+                              dev, dev + na, ctx->stream));
+    std::vector<double> host((size_t)na + 6);
+    CK(ctx, cudaMemcpyAsync(host.data(), dev, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    if (lbm_status fs = check_flag(ctx); fs != LBM_OK) return fs;
+    const double area = (double)ctx->c.nodes / na;
+    for (int j = 0; j < na; ++j) profile[j] = host[j] / area;
+    if (nu_mid)
+        for (int f = 0; f < 6; ++f) nu_mid[f] = host[(size_t)na + f];
     return LBM_OK;
 }
 
@@ -969,6 +1017,7 @@ lbm_status lbm_batch_create(lbm_ctx *const *cells, int ncells, void *stream, lbm
         lbm_ctx *x = cells[c];
         cd[c].G = x->G;
         cd[c].P = x->P;
+        cd[c].P.t = (uint32_t)x->step;
         cd[c].f = x->fbase(0);
         cd[c].g = x->gbase(0);
         cd[c].face = x->face;

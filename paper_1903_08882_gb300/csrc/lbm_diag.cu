@@ -85,76 +85,178 @@ struct KSum {
     __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 
+// Derivative from the values at the node and its two neighbours along an
+// axis, with the stencils of deriv(): wm / wp flag a wall behind the -1 / +1
+// neighbour, vlo / vhi a known wall value wlo / whi there.
+__device__ __forceinline__ float dval(float pm, float p0, float pp, bool wm, bool wp, bool vlo, float wlo, bool vhi,
+                                      float whi) {
+    if (!wm && !wp) return 0.5f * (pp - pm);
+    if (wm && wp) return 0.f;
+    if (wm) return vlo ? (-4.f / 3.f) * wlo + p0 + pp * (1.f / 3.f) : 0.5f * (pp - p0);
+    return vhi ? (4.f / 3.f) * whi - p0 - pm * (1.f / 3.f) : 0.5f * (p0 - pm);
+}
+
+// Diagnostic sums of one sample.  The lattice is cut into columns of
+// kDiagTX x kDiagTY nodes in x, y and segments of kDiagSeg planes in z; a
+// block takes one such brick at a time (bricks strided over the grid, so any
+// grid size works) and marches up its planes: each thread keeps the four
+// fields (u, v, w, T) of its own column at z - 1, z, z + 1 in registers for
+// the z derivatives, and the current plane goes through shared memory with
+// a one-node halo for the x and y derivatives.  Every field value is read
+// from memory about once (the halo and the two planes that start a segment
+// add ~15%).  Per-thread sums are compensated FP32 over at most kDiagSeg
+// nodes; the rare wall terms go into shared FP64 sums.
+constexpr int kDiagTX = 32, kDiagTY = kDiagThreads / kDiagTX, kDiagSeg = 32;
+
 __global__ void __launch_bounds__(kDiagThreads) k_diag(const float *__restrict__ mom, Geom G, Phys P,
                                                        WallT W, double *__restrict__ partial) {
     __shared__ double sh[kDiagThreads / 32][kNDiag];
-    KSum acc[kNDiag];
+    __shared__ float pl[4][kDiagTY + 2][kDiagTX + 2]; // u, v, w, T of the current plane, with halo
+    __shared__ double wall[12];                        // slots 8..13 and 18..23
+    const int tx = threadIdx.x % kDiagTX, ty = threadIdx.x / kDiagTX;
+    if (threadIdx.x < 12) wall[threadIdx.x] = 0.0;
+    KSum acc[10]; // slots 1..7, 14, 15 (acc[k] for slot k <= 7, acc[8] slot 14, acc[9] slot 15)
     float vmax = 0.f;
     uint32_t count = 0, bad = 0;
     const int64_t s = G.stride;
-    const float *dr = mom, *U = mom + s, *V = mom + 2 * s, *Wv = mom + 3 * s, *T = mom + 4 * s;
-    const float *phi[3] = {U, V, Wv};
-    for (uint32_t n = blockIdx.x * blockDim.x + threadIdx.x; n < G.n; n += gridDim.x * blockDim.x) {
-        int x, y, z;
-        node_xyz(G, n, x, y, z);
-        const Nbr b = neighbours(G, x, y, z);
-        const float d = dr[n], u = U[n], vv = V[n], w = Wv[n], t = T[n];
-        const float uu = u * u + vv * vv + w * w;
-        float du[3][3]; // du[i][j] = d u_j / d x_i
+    const float *F[4] = {mom + s, mom + 2 * s, mom + 3 * s, mom + 4 * s};
+    const float *dr = mom;
+    const int nx = G.nx, ny = G.ny, nz = G.nz;
+    const bool perx = G.periodic & 1, pery = (G.periodic >> 1) & 1, perz = (G.periodic >> 2) & 1;
+    const int bx = (nx + kDiagTX - 1) / kDiagTX, by = (ny + kDiagTY - 1) / kDiagTY, bz = (nz + kDiagSeg - 1) / kDiagSeg;
+    const int nbricks = bx * by * bz;
+    const bool dir[6] = {(P.dir_mask & 1) != 0, (P.dir_mask & 2) != 0, (P.dir_mask & 4) != 0,
+                         (P.dir_mask & 8) != 0, (P.dir_mask & 16) != 0, (P.dir_mask & 32) != 0};
+    __syncthreads();
+    for (int br = blockIdx.x; br < nbricks; br += gridDim.x) {
+        const int ib = br % bx, jb = (br / bx) % by, kb = br / (bx * by);
+        const int x = ib * kDiagTX + tx, y = jb * kDiagTY + ty;
+        const bool col = x < nx && y < ny;
+        const int z0 = kb * kDiagSeg, z1 = min(nz, z0 + kDiagSeg);
+        const uint32_t c = (uint32_t)(col ? x : 0) + (uint32_t)nx * (uint32_t)(col ? y : 0); // column offset
+        // registers: the column's fields at z - 1 (pm), z (p0), z + 1 (pp)
+        float pm[4], p0[4], pp[4];
+        const int zb = z0 > 0 ? z0 - 1 : (perz ? nz - 1 : 0);
 #pragma unroll
-        for (int i = 0; i < 3; ++i)
+        for (int q = 0; q < 4; ++q) {
+            pm[q] = col ? F[q][c + G.nxy * (uint32_t)zb] : 0.f;
+            p0[q] = col ? F[q][c + G.nxy * (uint32_t)z0] : 0.f;
+        }
+        for (int z = z0; z < z1; ++z) {
+            const bool zlo = z == 0 && !perz, zhi = z == nz - 1 && !perz;
+            const int zn = z + 1 < nz ? z + 1 : (perz ? 0 : z);
+            const uint32_t plane = G.nxy * (uint32_t)z;
 #pragma unroll
-            for (int j = 0; j < 3; ++j) du[i][j] = deriv(phi[j], n, b, i, true, 0.f, true, 0.f);
-        float gT[3];
+            for (int q = 0; q < 4; ++q) pp[q] = col ? F[q][c + G.nxy * (uint32_t)zn] : 0.f;
+            // the current plane into shared memory: own values, then the halo
 #pragma unroll
-        for (int i = 0; i < 3; ++i)
-            gT[i] = deriv(T, n, b, i, (P.dir_mask >> (2 * i)) & 1, W.Tw[2 * i],
-                          (P.dir_mask >> (2 * i + 1)) & 1, W.Tw[2 * i + 1]);
-        float eps = 0.f;
+            for (int q = 0; q < 4; ++q) pl[q][ty + 1][tx + 1] = p0[q];
+            if (ty == 0 || ty == kDiagTY - 1) { // rows y - 1 and y + kDiagTY (wrapped when y is periodic)
+                const int yh = ty == 0 ? jb * kDiagTY - 1 : jb * kDiagTY + kDiagTY;
+                const int yw = yh < 0 ? (pery ? ny - 1 : -1) : yh >= ny ? (pery ? yh - ny : -1) : yh;
+                const int r = ty == 0 ? 0 : kDiagTY + 1;
 #pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                const float sij = du[i][j] + du[j][i];
-                eps += 0.5f * sij * sij;
+                for (int q = 0; q < 4; ++q)
+                    pl[q][r][tx + 1] = (yw >= 0 && x < nx) ? F[q][(uint32_t)x + (uint32_t)nx * (uint32_t)yw + plane] : 0.f;
             }
-        const float dv = du[0][0] + du[1][1] + du[2][2];
-        count += 1;
-        acc[1].add(d * d);
-        acc[2].add(uu);
-        acc[3].add(w * w);
-        acc[4].add(w * t);
-        acc[5].add(eps);
-        acc[6].add(gT[0] * gT[0] + gT[1] * gT[1] + gT[2] * gT[2]);
-        acc[7].add(dv * dv);
-        acc[14].add(t);
-        acc[15].add(d); // sum rho = nodes + sum (rho - rho0)
-        vmax = fmaxf(vmax, sqrtf(uu));
-        if (!isfinite(uu) || !isfinite(t) || !isfinite(d)) bad += 1;
+            if (tx == 0 || tx == kDiagTX - 1) { // columns x - 1 and x + kDiagTX
+                const int xh = tx == 0 ? ib * kDiagTX - 1 : ib * kDiagTX + kDiagTX;
+                const int xw = xh < 0 ? (perx ? nx - 1 : -1) : xh >= nx ? (perx ? xh - nx : -1) : xh;
+                const int cc = tx == 0 ? 0 : kDiagTX + 1;
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
+                for (int q = 0; q < 4; ++q)
+                    pl[q][ty + 1][cc] = (xw >= 0 && y < ny) ? F[q][(uint32_t)xw + (uint32_t)nx * (uint32_t)y + plane] : 0.f;
+            }
+            __syncthreads();
+            if (col) {
+                const uint32_t n = c + plane;
+                const bool xlo = x == 0 && !perx, xhi = x == nx - 1 && !perx;
+                const bool ylo = y == 0 && !pery, yhi = y == ny - 1 && !pery;
+                // neighbour values along x and y from the plane buffer; the last node of
+                // a periodic axis that ends inside the tile reads its wrapped neighbour
+                // (node 0 of the axis) from memory
+                const bool wrapx = perx && x == nx - 1 && tx < kDiagTX - 1;
+                const bool wrapy = pery && y == ny - 1 && ty < kDiagTY - 1;
+                float du[3][3], gT[3];
 #pragma unroll
-            for (int side = 0; side < 2; ++side) {
-                const int fc = 2 * a + side;
-                const bool at = side == 0 ? b.wm[a] : b.wp[a];
-                if (!at || !((P.dir_mask >> fc) & 1)) continue;
-                const float t1 = T[(int64_t)n + (side == 0 ? b.op[a] : b.om[a])];
-                const float dTdn = (-8.f * W.Tw[fc] + 9.f * t - t1) * (1.f / 3.f);
-                acc[8 + fc].add(-dTdn);
-                const float gin = mom[(5 + fc) * s + n];
-                acc[18 + fc].add(2.f * gin - P.abbT[fc]);
+                for (int q = 0; q < 4; ++q) {
+                    const float xm = pl[q][ty + 1][tx];
+                    const float xp = wrapx ? F[q][(uint32_t)nx * (uint32_t)y + plane] : pl[q][ty + 1][tx + 2];
+                    const float ym = pl[q][ty][tx + 1];
+                    const float yp = wrapy ? F[q][(uint32_t)x + plane] : pl[q][ty + 2][tx + 1];
+                    if (q < 3) {
+                        du[0][q] = dval(xm, p0[q], xp, xlo, xhi, true, 0.f, true, 0.f);
+                        du[1][q] = dval(ym, p0[q], yp, ylo, yhi, true, 0.f, true, 0.f);
+                        du[2][q] = dval(pm[q], p0[q], pp[q], zlo, zhi, true, 0.f, true, 0.f);
+                    } else {
+                        gT[0] = dval(xm, p0[3], xp, xlo, xhi, dir[0], W.Tw[0], dir[1], W.Tw[1]);
+                        gT[1] = dval(ym, p0[3], yp, ylo, yhi, dir[2], W.Tw[2], dir[3], W.Tw[3]);
+                        gT[2] = dval(pm[3], p0[3], pp[3], zlo, zhi, dir[4], W.Tw[4], dir[5], W.Tw[5]);
+                    }
+                }
+                const float d = dr[n], u = p0[0], vv = p0[1], w = p0[2], t = p0[3];
+                const float uu = u * u + vv * vv + w * w;
+                float eps = 0.f;
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) {
+                        const float sij = du[i][j] + du[j][i];
+                        eps += 0.5f * sij * sij;
+                    }
+                const float dv = du[0][0] + du[1][1] + du[2][2];
+                count += 1;
+                acc[1].add(d * d);
+                acc[2].add(uu);
+                acc[3].add(w * w);
+                acc[4].add(w * t);
+                acc[5].add(eps);
+                acc[6].add(gT[0] * gT[0] + gT[1] * gT[1] + gT[2] * gT[2]);
+                acc[7].add(dv * dv);
+                acc[8].add(t);
+                acc[9].add(d); // sum rho = nodes + sum (rho - rho0)
+                vmax = fmaxf(vmax, sqrtf(uu));
+                if (!isfinite(uu) || !isfinite(t) || !isfinite(d)) bad += 1;
+                // Dirichlet faces: wall gradient and anti-bounce-back link flux
+                const bool at[6] = {xlo, xhi, ylo, yhi, zlo, zhi};
+#pragma unroll
+                for (int fc = 0; fc < 6; ++fc) {
+                    if (!at[fc] || !dir[fc]) continue;
+                    const int a = fc / 2;
+                    const float t1 = a == 0 ? pl[3][ty + 1][fc == 0 ? tx + 2 : tx]
+                                   : a == 1 ? pl[3][fc == 2 ? ty + 2 : ty][tx + 1]
+                                            : (fc == 4 ? pp[3] : pm[3]);
+                    const float dTdn = (-8.f * W.Tw[fc] + 9.f * t - t1) * (1.f / 3.f);
+                    atomicAdd(&wall[fc], (double)(-dTdn));
+                    const float gin = mom[(5 + fc) * s + n];
+                    atomicAdd(&wall[6 + fc], (double)(2.f * gin - P.abbT[fc]));
+                }
+            }
+            __syncthreads(); // the plane buffer is rewritten next
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                pm[q] = p0[q];
+                p0[q] = pp[q];
             }
         }
     }
     double v[kNDiag];
 #pragma unroll
-    for (int k = 0; k < kNDiag; ++k) v[k] = acc[k].value();
+    for (int k = 0; k < kNDiag; ++k) v[k] = 0.0;
+#pragma unroll
+    for (int k = 1; k <= 7; ++k) v[k] = acc[k].value();
+    v[14] = acc[8].value();
     v[0] = (double)count;
-    v[15] += (double)count;
+    v[15] = acc[9].value() + (double)count;
     v[16] = (double)vmax;
     v[17] = (double)bad;
     block_reduce(v, sh);
     if (threadIdx.x == 0) {
+#pragma unroll
+        for (int fc = 0; fc < 6; ++fc) {
+            v[8 + fc] = wall[fc];
+            v[18 + fc] = wall[6 + fc];
+        }
 #pragma unroll
         for (int k = 0; k < kNDiag; ++k) partial[(int64_t)blockIdx.x * kNDiag + k] = v[k];
     }
@@ -291,9 +393,125 @@ cudaError_t launch_eps_hist(const float *mom, const Geom &G, const Phys &P, cons
     return cudaGetLastError();
 }
 
+// Plane-averaged Nusselt number along axis a (Sec. 3, Nu(y) of Fig. 4):
+// adds, for every node, u_a T H/kappa - H dT/dx_a (stencils of k_diag) into
+// prof[j] of its plane j.  Sums per block in shared memory (FP64; SHARED =
+// false adds straight into global memory for axes too long for it), a warp
+// whose nodes share one plane adds its shuffled sum once.
+template <bool SHARED>
+__global__ void __launch_bounds__(kDiagThreads) k_nu_profile(const float *__restrict__ mom, Geom G, Phys P, WallT W,
+                                                             int axis, float hk, float H,
+                                                             double *__restrict__ prof) {
+    extern __shared__ double acc[];
+    const int na = axis == 0 ? G.nx : axis == 1 ? G.ny : G.nz;
+    double *out = SHARED ? acc : prof;
+    if (SHARED) {
+        for (int i = threadIdx.x; i < na; i += blockDim.x) acc[i] = 0.0;
+        __syncthreads();
+    }
+    const int64_t s = G.stride;
+    const float *ua = mom + (1 + axis) * s, *T = mom + 4 * s;
+    const int lane = threadIdx.x & 31;
+    const uint32_t step = gridDim.x * blockDim.x;
+    for (uint32_t base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < G.n; base += step) {
+        const uint32_t n = base + (uint32_t)lane;
+        const bool valid = n < G.n;
+        double v = 0.0;
+        int j = -1;
+        if (valid) {
+            int x, y, z;
+            node_xyz(G, n, x, y, z);
+            const Nbr b = neighbours(G, x, y, z);
+            const float dT = deriv(T, n, b, axis, (P.dir_mask >> (2 * axis)) & 1, W.Tw[2 * axis],
+                                   (P.dir_mask >> (2 * axis + 1)) & 1, W.Tw[2 * axis + 1]);
+            v = (double)(ua[n] * T[n] * hk - H * dT);
+            j = axis == 0 ? x : axis == 1 ? y : z;
+        }
+        const int j0 = __shfl_sync(0xffffffffu, j, 0);
+        if (__all_sync(0xffffffffu, j == j0 || !valid)) {
+            v = warp_sum(v);
+            if (lane == 0) atomicAdd(&out[j0], v);
+        } else if (valid) {
+            atomicAdd(&out[j], v);
+        }
+    }
+    if (SHARED) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < na; i += blockDim.x)
+            if (acc[i] != 0.0) atomicAdd(&prof[i], acc[i]);
+    }
+}
+
+// Mid-line wall Nusselt numbers (Sec. 3, Nu_mean of Table 2): block f takes
+// face f and writes mid[f] = the mean of -H dT/dn at the wall (one-sided
+// stencil of k_diag) over the nodes next to the face on the line along z
+// (along x for the z faces) through the middle of the third axis: one node
+// line for an odd node count, the two bracketing lines for an even one.
+// 0 for faces that are not Dirichlet walls.
+__global__ void __launch_bounds__(kDiagThreads) k_nu_midline(const float *__restrict__ mom, Geom G, Phys P,
+                                                             WallT W, float H, double *__restrict__ mid) {
+    __shared__ double sh[kDiagThreads / 32];
+    const int fc = blockIdx.x;
+    if (!((P.dir_mask >> fc) & 1)) {
+        if (threadIdx.x == 0) mid[fc] = 0.0;
+        return;
+    }
+    const int nn[3] = {G.nx, G.ny, G.nz};
+    const int b = fc / 2, hi = fc % 2, l = b == 2 ? 0 : 2, m = 3 - b - l;
+    const int m0 = (nn[m] - 1) / 2, lines = nn[m] % 2 ? 1 : 2;
+    const int count = lines * nn[l];
+    const float *T = mom + 4 * G.stride;
+    double acc = 0.0;
+    for (int k = threadIdx.x; k < count; k += blockDim.x) {
+        int c0[3], c1[3];
+        c0[b] = hi ? nn[b] - 1 : 0;
+        c1[b] = hi ? nn[b] - 2 : 1;
+        c0[l] = c1[l] = k % nn[l];
+        c0[m] = c1[m] = m0 + k / nn[l];
+        const float t0 = T[(uint32_t)c0[0] + (uint32_t)G.nx * ((uint32_t)c0[1] + (uint32_t)G.ny * (uint32_t)c0[2])];
+        const float t1 = T[(uint32_t)c1[0] + (uint32_t)G.nx * ((uint32_t)c1[1] + (uint32_t)G.ny * (uint32_t)c1[2])];
+        acc += (double)(-H * (-8.f * W.Tw[fc] + 9.f * t0 - t1) * (1.f / 3.f));
+    }
+    acc = warp_sum(acc);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (lane == 0) sh[wid] = acc;
+    __syncthreads();
+    if (wid == 0) {
+        acc = warp_sum(lane < nw ? sh[lane] : 0.0);
+        if (lane == 0) mid[fc] = acc / count;
+    }
+}
+
+constexpr int kProfileSharedMax = 6144; // axis length held in shared memory (48 KB)
+
+cudaError_t launch_nu_profile(const float *mom, const Geom &G, const Phys &P, const float *wallT, int axis,
+                              float H, float kappa, double *prof, double *mid, cudaStream_t stream) {
+    WallT W;
+    for (int k = 0; k < 6; ++k) W.Tw[k] = wallT[k];
+    const int na = axis == 0 ? G.nx : axis == 1 ? G.ny : G.nz;
+    if (na <= kProfileSharedMax)
+        k_nu_profile<true><<<diag_blocks(G), kDiagThreads, (size_t)na * sizeof(double), stream>>>(
+            mom, G, P, W, axis, H / kappa, H, prof);
+    else
+        k_nu_profile<false><<<diag_blocks(G), kDiagThreads, 0, stream>>>(mom, G, P, W, axis, H / kappa, H, prof);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_nu_midline<<<6, kDiagThreads, 0, stream>>>(mom, G, P, W, H, mid);
+    return cudaGetLastError();
+}
+
 int diag_blocks(const Geom &G) {
-    const int64_t need = ((int64_t)G.n + kDiagThreads - 1) / kDiagThreads;
-    return (int)(need < 152 * 8 ? need : 152 * 8);
+    // bricks of the diagnostics kernel, at most 8 blocks per SM of the current device
+    const int64_t need = (int64_t)((G.nx + kDiagTX - 1) / kDiagTX) * ((G.ny + kDiagTY - 1) / kDiagTY) *
+                         ((G.nz + kDiagSeg - 1) / kDiagSeg);
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess || nsm < 1) {
+        cudaGetLastError();
+        nsm = 152;
+    }
+    const int64_t cap = 8 * (int64_t)nsm;
+    return (int)(need < cap ? need : cap);
 }
 
 cudaError_t launch_diag(const float *mom, const Geom &G, const Phys &P, const float *wallT,

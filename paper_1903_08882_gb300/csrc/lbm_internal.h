@@ -60,6 +60,10 @@ cudaError_t launch_gather(int storage, float *out, const int64_t *nodes, int64_t
                           const void *g, const Geom &G, const Phys &P, int layout, cudaStream_t stream);
 cudaError_t launch_equilibrium(float *st, const float *fields, uint32_t n, const Phys &P,
                                cudaStream_t stream);
+// Equilibrium of device FP64 fields rho[n], u3[3][n], T[n] straight into the
+// natural device layout (AA before an even step).
+cudaError_t launch_fields_natural(int storage, const double *rho, const double *u3, const double *T, void *f,
+                                  void *g, const Geom &G, const Phys &P, cudaStream_t stream);
 
 // Diagnostics: reduce the moment arrays into per-block partial sums, then sum
 // them into raw[kNDiag] (this sample) and add raw to acc[kNDiag] (time sums;
@@ -74,13 +78,18 @@ cudaError_t launch_eps_sq(const float *mom, const Geom &G, const Phys &P, const 
 cudaError_t launch_eps_hist(const float *mom, const Geom &G, const Phys &P, const float *wallT, float nu,
                             float ka, double scale_u, double scale_t, int nbins, unsigned long long *counts,
                             cudaStream_t stream);
+// Nusselt profile along axis (Sec. 3, Fig. 4) into prof[n_axis] (sums over
+// each plane, added; the caller zeroes and divides by the plane's node count)
+// and the six mid-line wall Nusselt numbers (Sec. 3, Table 2) into mid[6].
+cudaError_t launch_nu_profile(const float *mom, const Geom &G, const Phys &P, const float *wallT, int axis,
+                              float H, float kappa, double *prof, double *mid, cudaStream_t stream);
 cudaError_t launch_diag(const float *mom, const Geom &G, const Phys &P, const float *wallT,
                         double *partial, int nblocks, double *raw, double *acc, cudaStream_t stream);
 
 // ---- batched persistent launch ----
 struct CellDev {
     Geom G;
-    Phys P;
+    Phys P;               // P.t: the cell's time step when the batch was created
     void *f, *g;          // AA population buffer of the cell (f arrays, then g arrays)
     const uint32_t *face; // nodes next to a face
     uint32_t nface;
@@ -92,8 +101,8 @@ struct Tile {
 };
 struct GridBarrier {
     unsigned count, gen;
-    int err; // 1: a wait ran out of its cycle budget
-    int pad;
+    int err;        // 1: a wait ran out of its cycle budget
+    unsigned steps; // time steps the batch has taken (device-side, so graph replays advance it)
 };
 struct BatchArgs {
     const CellDev *cells;
@@ -107,6 +116,11 @@ struct BatchArgs {
 // block is 128 or 256 threads (two compiled variants)
 const void *batch_kernel_ptr(int storage, int block);
 cudaError_t launch_batch(int storage, const BatchArgs &a);
+
+// Loads, on the current device, the static scratch of lbm_reduce_noalloc
+// (see lbm_noalloc.cu); lbm_create calls it so that the array is taken at
+// set-up rather than at a later no-allocation call.
+cudaError_t noalloc_setup();
 
 // Sets the message lbm_last_error(NULL) returns.
 void set_global_error(const std::string &msg);

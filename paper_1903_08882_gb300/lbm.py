@@ -114,6 +114,7 @@ def lib():
         "lbm_moments": ([c_void_p, dp, dp, dp], c_int),
         "lbm_sample": ([c_void_p], c_int),
         "lbm_dissipation_pdf": ([c_void_p, c_int, c_double, dp, dp, P(ctypes.c_uint64), P(ctypes.c_uint64)], c_int),
+        "lbm_nusselt_profile": ([c_void_p, c_int, dp, dp], c_int),
         "lbm_diagnostics": ([c_void_p, P(LbmDiag), c_int], c_int),
         "lbm_synchronize": ([c_void_p], c_int),
         "lbm_set_wait_budget": ([c_void_p, c_int64], c_int),
@@ -325,6 +326,17 @@ def lbm_dissipation_pdf(ctx, nbins: int = 200, xmax: float = 20.0, rms=None):
     return cu, ct, (float(out[0]), float(out[1]))
 
 
+def lbm_nusselt_profile(ctx, shape, axis: int = 0):
+    """Plane-averaged Nusselt number along `axis` and the six mid-line wall
+    Nusselt numbers (Sec. 3: Nu(y) of Fig. 4, Nu_mean of Table 2) of the
+    current state; shape = (nz, ny, nx).  Returns (profile, nu_mid)."""
+    na = (shape[2], shape[1], shape[0])[int(axis)]
+    prof = np.zeros(na)
+    mid = np.zeros(6)
+    _check(ctx, lib().lbm_nusselt_profile(ctx, int(axis), _dp(prof), _dp(mid)))
+    return prof, mid
+
+
 def lbm_sample(ctx):
     _check(ctx, lib().lbm_sample(ctx))
 
@@ -523,6 +535,9 @@ class Lattice:
 
     def dissipation_pdf(self, nbins=200, xmax=20.0, rms=None):
         return lbm_dissipation_pdf(self.ctx, nbins, xmax, rms)
+
+    def nusselt_profile(self, axis=0):
+        return lbm_nusselt_profile(self.ctx, self.shape, axis)
 
     def diagnostics(self, reset=False, raise_on_diverged=True):
         return lbm_diagnostics(self.ctx, reset, raise_on_diverged)
