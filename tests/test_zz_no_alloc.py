@@ -7,7 +7,9 @@ context allocated.  This file is collected last on purpose.  Each check
 builds the reduction's input fields on the device from a context's own
 state, calls the entry point through the C ABI twice in a row on different
 states, and compares the sums with those lbm_sample produced for the same
-state, within the tolerance of the other diagnostics tests (1e-5)."""
+state, within the tolerance of the other diagnostics tests (1e-5).  The
+device's free memory is read before and after each call: creating the
+context already loaded the static array, so neither call may take any."""
 import numpy as np
 import pytest
 
@@ -61,9 +63,11 @@ def test_noalloc_reduction_matches_context_path():
             fields = _device_fields(torch, lat, stride)
             sums.fill_(np.nan)
             torch.cuda.synchronize()
+            free_before = torch.cuda.mem_get_info()[0]
             lbm.lbm_reduce_noalloc(fields.data_ptr(), stride, *n, walls, a_T, sums.data_ptr(),
                                    stream=torch.cuda.current_stream())
             torch.cuda.synchronize()
+            assert torch.cuda.mem_get_info()[0] == free_before, call
             got = sums.cpu().numpy()
             assert np.isfinite(got).all()
             assert np.allclose(got, ref, rtol=1e-5, atol=1e-12), (call, got - ref)
