@@ -199,25 +199,45 @@ def _cpu_oracle_rate(max_seconds=15.0, min_steps=2):
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle (the test reference, as it stands)
+    on the host cores.  Each benchmark step is a bounded sample of the
+    workload: `lb` oracle LB steps of a 257 x 257 x 8 slab of the 257^3
+    side-heated cell (same walls and parameters), lb chosen once so that a
+    step takes about 2 s.  ms_per_step is the time those steps took."""
     # the oracle runs on the host: rank 0 alone times it, the other ranks of a
     # multi-rank launch exit without work (no process group is needed)
     if int(os.environ.get("RANK", "0")) != 0:
         return
-    per_step, threads = [], None
-    for k in range(args.warmup + args.steps):
-        rate, threads, sample = _cpu_oracle_rate(max_seconds=2.0, min_steps=1)
-        if k >= args.warmup:
-            per_step.append(rate)
-    value = statistics.mean(per_step)
+    import oracle
+
+    oracle.build()
+    nz = 8
+    p = oracle.cell((N_EDGE, N_EDGE, nz), RA, PR, oracle.side_heated_walls(), H=N_EDGE)
+    f, g = oracle.init_equilibrium(p, 1.0, np.zeros(3), 0.0)
+    f, g = oracle.run(p, f, g, 1)  # warms the pages
+    t0 = time.perf_counter()
+    f, g = oracle.run(p, f, g, 2)
+    lb = max(1, int(round(2.0 / max((time.perf_counter() - t0) / 2, 1e-3))))
+    for _ in range(args.warmup):
+        f, g = oracle.run(p, f, g, lb)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f, g = oracle.run(p, f, g, lb)
+    el = time.perf_counter() - t0
+    nodes = N_EDGE * N_EDGE * nz
+    value = nodes * lb * args.steps / el / 1e9
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    workload = (f"{N_EDGE}x{N_EDGE}x{nz} slab of the side-heated 257^3 cell (Ra=1e7, Pr=0.71, U=0.1), "
+                f"{lb} FP64 oracle LB steps per benchmark step")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "GLUPS", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup,
-        # one benchmark step (CHUNK LB steps of the whole cube) at the sampled rate
-        "ms_per_step": round(CHUNK * N_EDGE ** 3 / (value * 1e9) * 1e3, 1),
+        "ms_per_step": round(el / args.steps * 1e3, 1),
         "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "side-heated cube 257^3, Ra=1e7, Pr=0.71, U=0.1 (bounded slab sample)"},
-        "cpu_baseline": {"value": value, "unit": "GLUPS", "cores": threads, "kind": "oracle", "sample": sample},
+        "config": {"workload": workload, "lb_steps_per_step": lb, "nodes": nodes},
+        "cpu_baseline": {"value": value, "unit": "GLUPS", "cores": threads, "kind": "oracle",
+                         "sample": f"{workload}; {args.steps} timed steps, {el:.1f} s"},
         "e2e": {"value": value, "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -256,6 +276,62 @@ def _step_kernel_seconds(lat, stream, launches=98):
     return ev[0].elapsed_time(ev[launches]) / 1e3 / launches, even[len(even) // 2], odd[len(odd) // 2]
 
 
+def _event_ms(fn, stream, reps=10):
+    """Mean duration of fn() over reps calls, CUDA events on `stream`."""
+    import torch
+
+    fn()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(reps):
+        fn()
+    ev1.record(stream)
+    ev1.synchronize()
+    return ev0.elapsed_time(ev1) / reps
+
+
+def bench_diagnostics(lbm, lat, stream, peak):
+    """Timing of the diagnostics of one state of the benchmark cell (Secs. 3-4):
+    the reduction kernel alone (k_diag + its one-block finish, run through
+    lbm_reduce_noalloc on the moment arrays of the state), a whole sample
+    (moments of the state, then the reduction), the dissipation-rate PDFs and
+    the Nusselt profile with the mid-line wall values."""
+    import torch
+
+    N = N_EDGE
+    n = N ** 3
+    stride = (n + 127) // 128 * 128
+    rho, u3, T = lat.moments()
+    fields = torch.zeros((11, stride), dtype=torch.float32)
+    fields[0, :n] = torch.from_numpy((rho - 1.0).ravel().astype(np.float32))
+    for a in range(3):
+        fields[1 + a, :n] = torch.from_numpy(u3[a].ravel().astype(np.float32))
+    fields[4, :n] = torch.from_numpy(T.ravel().astype(np.float32))
+    fields = fields.cuda()
+    sums = torch.zeros(24, dtype=torch.float64, device="cuda")
+    walls, a_T = lbm.walls_side_heated(), lat.constants["a_T"]
+    red = _event_ms(lambda: lbm.lbm_reduce_noalloc(fields.data_ptr(), stride, N, N, N, walls, a_T,
+                                                   sums.data_ptr(), stream=stream), stream)
+    in_bytes = 5 * 4 * n  # rho - rho0, u, v, w, T once each (neighbours from cache)
+    ach = in_bytes / (red * 1e-3) / 1e9
+    sample = _event_ms(lat.sample, stream)
+    t0 = time.perf_counter()
+    for _ in range(3):
+        lat.dissipation_pdf(nbins=200, xmax=20.0)
+    pdf = (time.perf_counter() - t0) / 3 * 1e3
+    t0 = time.perf_counter()
+    for _ in range(3):
+        lat.nusselt_profile(axis=0)
+    prof = (time.perf_counter() - t0) / 3 * 1e3
+    del fields, sums
+    return {"reduction": {"kernel": "k_diag + k_diag_finish", "ms": round(red, 4), "input_bytes": in_bytes,
+                          "achieved_gbs": round(ach, 1), "frac_of_peak": round(ach / peak, 4)},
+            "sample_ms": round(sample, 4),
+            "sample_what": "moments of the state (k_moments) then the reduction",
+            "dissipation_pdf_ms": round(pdf, 3), "nusselt_profile_ms": round(prof, 3),
+            "host_synchronous": "dissipation_pdf and nusselt_profile include their host read-back"}
+
+
 def bench_storage(lbm, storage, args, stream, dist, with_e2e):
     import torch
 
@@ -282,6 +358,7 @@ def bench_storage(lbm, storage, args, stream, dist, with_e2e):
         res["Nu_hot"] = float(d["Nu_face"][0])
         res["diverged"] = bool(d["diverged"])
         if with_e2e:
+            res["diagnostics"] = bench_diagnostics(lbm, lat, stream, _peak_hbm()[0])
             res["e2e"] = _e2e(lbm, lat, args, stream, dist)
     finally:
         lat.close()
@@ -428,6 +505,7 @@ def run_gpu(args):
                                   "roofline": roof(r, st), "clocks": r["clocks"],
                                   "speedup_vs_fp32": round(r["glups"] / main["glups"], 3)}
                              for st, r in results.items() if st != "fp32"},
+        "diagnostics": main.get("diagnostics"),
         "Nu_hot_after_run": main["Nu_hot"],
         "batched_sweep": batched,
     }

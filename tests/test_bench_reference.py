@@ -1,6 +1,7 @@
 """The benchmark's reference arm (the FP64 oracle on the host cores) runs
-without a GPU and prints one JSON line of the benchmark's form; under a
-multi-rank launch only rank 0 works and prints."""
+without a GPU and prints one JSON line of the benchmark's form, with the
+per-step time it actually measured on the slab it names; under a multi-rank
+launch only rank 0 works and prints."""
 import json
 import os
 import subprocess
@@ -29,8 +30,11 @@ def test_reference_arm_prints_one_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"] == {"value": d["value"], "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
-    # one benchmark step is 100 LB steps of the 257^3 cube
-    assert abs(d["ms_per_step"] - 100 * 257 ** 3 / (d["value"] * 1e9) * 1e3) <= 0.05 + 1e-6 * d["ms_per_step"]
+    # one benchmark step is lb oracle steps of the named slab, and ms_per_step is
+    # the time that step took: consistent with the rate
+    lb, nodes = d["config"]["lb_steps_per_step"], d["config"]["nodes"]
+    assert nodes == 257 * 257 * 8 and lb >= 1 and "slab" in d["config"]["workload"]
+    assert abs(d["ms_per_step"] - lb * nodes / (d["value"] * 1e9) * 1e3) <= 0.05 + 1e-3 * d["ms_per_step"]
 
 
 def test_reference_arm_other_ranks_exit_quietly():

@@ -1,15 +1,22 @@
 """What the trained warm-start network gains over the method without it.
 
-Two held-out (Ra, Pr) pairs of the side-heated cell at 65^3 (never seen in
-training): the first draw of the held-out stream and (1e6, 0.71).  Each runs
-to the steady criterion (relative change of the hot-wall Nu below 1e-7 over
-1000 steps) from rest and from the network's prediction (stored weights),
-and both runs must land on the same Nu.  Over the whole held-out evaluation
-(32 pairs) the network start took 1.67x fewer steps on the geometric mean,
-up to 7.75x and 0.82x on the worst pair: the iteration's slow relaxation
-mode, which a prediction accurate to ~0.1% in Nu removes only where the
-network is most accurate, sets the remaining steps.  On these two pairs it
-took 3.24x and 1.04x fewer."""
+The held-out (Ra, Pr) pairs are fixed in advance, independently of how the
+network does on them: the first six draws of the held-out stream (never
+seen in training) and (1e6, 0.71), the case the FP64 oracle has a 65^3
+steady state for.  Each runs at 65^3 to the steady criterion (relative
+change of the hot-wall Nu below 1e-7 over 1000 steps) from rest and from
+the network's prediction (stored weights).  Checked:
+  - every run converges, and both starts of a pair land on the same Nu
+    (1e-4, the criterion's resolution);
+  - the (1e6, 0.71) runs end within 0.1% (the steady-Nu bound of FP32
+    storage) of the oracle's steady Nu at 65^3
+    (tests/golden/steady_side_heated_65.json);
+  - over the fixed set the network start needs fewer steps than rest on
+    the geometric mean (the 32-pair evaluation: 1.67x, 14 pairs gaining
+    1.75x-7.75x and 18 losing 3-18%: the iteration's slow relaxation mode,
+    which a prediction accurate to ~0.1% in Nu removes only where the
+    network is most accurate, sets the remaining steps)."""
+import json
 import os
 
 import numpy as np
@@ -19,8 +26,8 @@ torch = pytest.importorskip("torch")
 
 pytestmark = pytest.mark.gpu
 
-WEIGHTS = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_1903_08882_gb300",
-                       "warmstart_unet_65.npz")
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+WEIGHTS = os.path.join(ROOT, "paper_1903_08882_gb300", "warmstart_unet_65.npz")
 
 
 @pytest.fixture(scope="module")
@@ -39,7 +46,9 @@ def test_network_start_against_cold_start(ws):
     from paper_1903_08882_gb300 import inputs
 
     pairs = inputs.warmstart_pairs(190308882, 400 + 8 + 64)
-    held_out = [pairs[400], (1e6, 0.71)]
+    held_out = list(pairs[400:406]) + [(1e6, 0.71)]
+    with open(os.path.join(ROOT, "tests", "golden", "steady_side_heated_65.json")) as fh:
+        oracle_nu = json.load(fh)["Nu_hot"]
     stream = torch.cuda.Stream()
     speedups = []
     with torch.cuda.stream(stream):
@@ -51,9 +60,10 @@ def test_network_start_against_cold_start(ws):
             pred = trainer.predict(trainer.make_input(c, Ra, Pr))
             cold = ws.run_from(Ra, Pr, None, stream)
             warm = ws.run_from(Ra, Pr, pred, stream)
-            assert cold["converged"] and warm["converged"]
-            # same steady state at the criterion's resolution
+            assert cold["converged"] and warm["converged"], (Ra, Pr)
             assert abs(warm["Nu"] - cold["Nu"]) <= 1e-4 * cold["Nu"], (Ra, Pr, warm["Nu"], cold["Nu"])
             speedups.append(cold["steps"] / warm["steps"])
-    assert speedups[0] >= 2.0, speedups
-    assert np.exp(np.mean(np.log(speedups))) > 1.2, speedups
+        assert abs(warm["Nu"] - oracle_nu) <= 1e-3 * oracle_nu, (warm["Nu"], oracle_nu)
+        assert abs(cold["Nu"] - oracle_nu) <= 1e-3 * oracle_nu, (cold["Nu"], oracle_nu)
+    geo = float(np.exp(np.mean(np.log(speedups))))
+    assert geo > 1.0, speedups
