@@ -269,9 +269,11 @@ lbm_status lbm_load(lbm_ctx *ctx, const char *path);
 /* Device view of the population storage, for callers that keep data on the
  * GPU: base pointers of f (19 arrays) and g (7 arrays), elements between
  * consecutive population arrays, and the element size in bytes of f (g uses
- * 4 bytes with LBM_FP16M, else the size of f).  The layout
- * of the values depends on the streaming scheme and on the step parity; use
- * lbm_get_populations to read them in a defined layout. */
+ * 4 bytes with LBM_FP16M, else the size of f).  Stored values are deviations
+ * from the rest state, f - w rho0 and g - w T0; with LBM_FP16S the g arrays
+ * hold 4096 (g - w T0) (scaled to keep small values out of FP16's subnormal
+ * range).  The layout of the values depends on the streaming scheme and on
+ * the step parity; use lbm_get_populations to read them in a defined layout. */
 lbm_status lbm_device_view(lbm_ctx *ctx, void **f, void **g, int64_t *stride, int *elem_bytes);
 
 /* ------------------------------------------------------------------ batches --
@@ -286,12 +288,17 @@ lbm_status lbm_device_view(lbm_ctx *ctx, void **f, void **g, int64_t *stride, in
 typedef struct lbm_batch lbm_batch;
 
 /* Schedule of the persistent launch (a new batch starts at 256 threads, 2 blocks
- * per SM, 100 steps per launch, 1000-step graphs). */
+ * per SM, 100 steps per launch, 1000-step graphs, tiles of one block, mode 0). */
 typedef struct {
     int block_size;    /* 128 or 256 threads */
     int blocks_per_sm; /* resident blocks per SM (capped by occupancy); grid = SMs x this */
     int steps_per_launch; /* time steps inside one launch (a launch boundary also synchronises) */
     int graph_chunk;   /* steps per captured graph (a multiple of steps_per_launch, even); 0 = no graph */
+    int tile_span;     /* tile shape: consecutive blocks of one cell's kernel per tile, 1..64 (a block
+                          fetches a tile's description once and updates its span in a row) */
+    int mode;          /* 0: one cooperative launch per steps_per_launch steps, a grid-wide barrier
+                          between steps; 1: one persistent launch per time step and tile kind (even
+                          tiles; row tiles, then face tiles), ordered by the launches themselves */
 } lbm_schedule;
 
 /* Create a batch over `ncells` contexts (borrowed: they must outlive the
@@ -313,9 +320,10 @@ lbm_status lbm_batch_step(lbm_batch *batch, int64_t n);
 lbm_status lbm_batch_get_schedule(const lbm_batch *batch, lbm_schedule *out);
 lbm_status lbm_batch_set_schedule(lbm_batch *batch, const lbm_schedule *s);
 
-/* Time each candidate schedule (block size 128/256, 1-3 blocks per SM) over
- * `trial_steps` steps and keep the fastest; the trials advance the cells.
- * *best receives it when non-NULL. */
+/* Time each candidate schedule (both modes, block size 128/256, 1-4 blocks per
+ * SM as they fit, tile spans 1, 2, 4, 8 and 16) over `trial_steps` steps and
+ * keep the fastest; the trials advance the cells.  *best receives it when
+ * non-NULL. */
 lbm_status lbm_batch_autotune(lbm_batch *batch, int trial_steps, lbm_schedule *best);
 
 /* Cycle budget of one grid-barrier wait (default 2^31 cycles, about a second).

@@ -441,6 +441,7 @@ lbm_status lbm_create(const lbm_params *params, const lbm_allocator *alloc, void
             T.mag_tpp = magic_of(T.tpp);
             T.odd_tiles = T.tpp * (uint32_t)(G.nz - 2);
             T.grid = nsm * per_sm; // persistent: every block resident
+            T.xf = G.nx >= staged_xf_min_nx() ? 1 : 0;
             T.budget = 1ll << 31;
             ctx->staged = true;
         }
@@ -872,13 +873,14 @@ struct lbm_batch {
     int dev = 0;
     int nsm = 0;
     cudaStream_t stream = nullptr;
-    lbm_schedule sched{256, 2, 100, 1000};
+    lbm_schedule sched{256, 2, 100, 1000, 1, 0};
     long long budget = 1LL << 31;
     CellDev *d_cells = nullptr;
     Tile *d_tiles = nullptr; // even tiles, then odd tiles
     size_t tiles_bytes = 0;
     GridBarrier *d_bar = nullptr;
-    int n_even = 0, n_odd = 0, tiles_block = 0;
+    int n_even = 0, n_odd = 0, n_rows = 0, n_faces = 0, tiles_block = 0, tiles_span = 0;
+    int grid_k[3] = {0, 0, 0}; // per-step mode: grid of each tile kind's kernel
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     lbm_schedule graph_sched{};
@@ -910,22 +912,25 @@ void drop_graph(lbm_batch *b) {
     b->graph_parity = -1;
 }
 
-// Tile lists for a block size: per cell, the blocks of its single-cell kernels.
-lbm_status build_tiles(lbm_batch *b, int block) {
-    std::vector<Tile> even, odd;
+// Tile lists for a block size and tile span: per cell, runs of `span`
+// consecutive blocks of its single-cell kernels; stored as even tiles, row
+// tiles, face tiles (the odd step's list is the last two together).
+lbm_status build_tiles(lbm_batch *b, int block, int span) {
+    std::vector<Tile> even, rows, faces;
     for (int c = 0; c < (int)b->cells.size(); ++c) {
         const lbm_ctx *x = b->cells[c];
         const Geom &G = x->G;
         const uint32_t ne = (uint32_t)(((uint64_t)G.n + 1) / 2 + block - 1) / block;
-        for (uint32_t k = 0; k < ne; ++k) even.push_back({c, TILE_EVEN, k});
+        const uint32_t sp = (uint32_t)span;
+        for (uint32_t k = 0; k < ne; k += sp) even.push_back({c, TILE_EVEN, k, ne - k < sp ? ne - k : sp});
         const uint64_t warps = (uint64_t)G.cpp * (uint64_t)(G.nz - 2);
         const uint32_t nr = (uint32_t)((warps + block / 32 - 1) / (block / 32));
-        for (uint32_t k = 0; k < nr; ++k) odd.push_back({c, TILE_ROWS, k});
+        for (uint32_t k = 0; k < nr; k += sp) rows.push_back({c, TILE_ROWS, k, nr - k < sp ? nr - k : sp});
         // the row tiles cover the x faces of their rows; the y/z-face nodes remain
         const uint32_t nf = (x->nface_yz + block - 1) / block;
-        for (uint32_t k = 0; k < nf; ++k) odd.push_back({c, TILE_FACE, k});
+        for (uint32_t k = 0; k < nf; k += sp) faces.push_back({c, TILE_FACE, k, nf - k < sp ? nf - k : sp});
     }
-    const size_t bytes = (even.size() + odd.size()) * sizeof(Tile);
+    const size_t bytes = (even.size() + rows.size() + faces.size()) * sizeof(Tile);
     lbm_ctx *a = b->cells[0];
     if (bytes > b->tiles_bytes) {
         cudaStreamSynchronize(b->stream);
@@ -934,23 +939,33 @@ lbm_status build_tiles(lbm_batch *b, int block) {
         b->tiles_bytes = b->d_tiles ? bytes : 0;
         if (!b->d_tiles) return bfail(b, LBM_ERR_OOM, "tile table allocation failed");
     }
-    BCK(b, cudaMemcpyAsync(b->d_tiles, even.data(), even.size() * sizeof(Tile), cudaMemcpyHostToDevice, b->stream));
-    BCK(b, cudaMemcpyAsync(b->d_tiles + even.size(), odd.data(), odd.size() * sizeof(Tile), cudaMemcpyHostToDevice,
-                           b->stream));
+    Tile *d = b->d_tiles;
+    BCK(b, cudaMemcpyAsync(d, even.data(), even.size() * sizeof(Tile), cudaMemcpyHostToDevice, b->stream));
+    d += even.size();
+    BCK(b, cudaMemcpyAsync(d, rows.data(), rows.size() * sizeof(Tile), cudaMemcpyHostToDevice, b->stream));
+    d += rows.size();
+    BCK(b, cudaMemcpyAsync(d, faces.data(), faces.size() * sizeof(Tile), cudaMemcpyHostToDevice, b->stream));
     BCK(b, cudaStreamSynchronize(b->stream));
     b->n_even = (int)even.size();
-    b->n_odd = (int)odd.size();
+    b->n_rows = (int)rows.size();
+    b->n_faces = (int)faces.size();
+    b->n_odd = b->n_rows + b->n_faces;
     b->tiles_block = block;
+    b->tiles_span = span;
+    return LBM_OK;
+}
+
+// Resident blocks per SM of a kernel at a block size, capped by the schedule.
+lbm_status blocks_for_kernel(lbm_batch *b, const void *fn, const lbm_schedule &s, int *grid) {
+    int occ = 0;
+    BCK(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, s.block_size, 0));
+    if (occ < 1) return bfail(b, LBM_ERR_PARAM, "batched kernel does not fit on an SM with this block size");
+    *grid = b->nsm * (s.blocks_per_sm < occ ? s.blocks_per_sm : occ);
     return LBM_OK;
 }
 
 lbm_status grid_for(lbm_batch *b, const lbm_schedule &s, int *grid) {
-    int occ = 0;
-    BCK(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel_ptr(b->storage, s.block_size),
-                                                        s.block_size, 0));
-    if (occ < 1) return bfail(b, LBM_ERR_PARAM, "batched kernel does not fit on an SM with this block size");
-    *grid = b->nsm * (s.blocks_per_sm < occ ? s.blocks_per_sm : occ);
-    return LBM_OK;
+    return blocks_for_kernel(b, batch_kernel_ptr(b->storage, s.block_size), s, grid);
 }
 
 BatchArgs batch_args(lbm_batch *b, int grid, int nsteps, int parity0) {
@@ -958,14 +973,20 @@ BatchArgs batch_args(lbm_batch *b, int grid, int nsteps, int parity0) {
     a.cells = b->d_cells;
     a.even = b->d_tiles;
     a.odd = b->d_tiles + b->n_even;
+    a.rows = a.odd;
+    a.faces = a.odd + b->n_rows;
     a.n_even = b->n_even;
     a.n_odd = b->n_odd;
+    a.n_rows = b->n_rows;
+    a.n_faces = b->n_faces;
     a.nsteps = nsteps;
     a.parity0 = parity0;
     a.bar = b->d_bar;
     a.budget = b->budget;
+    a.mode = b->sched.mode;
     a.grid = grid;
     a.block = b->sched.block_size;
+    for (int k = 0; k < 3; ++k) a.grid_k[k] = b->grid_k[k];
     a.stream = b->stream;
     return a;
 }
@@ -974,6 +995,8 @@ lbm_status check_schedule(lbm_batch *b, const lbm_schedule &s) {
     if (s.block_size != 128 && s.block_size != 256) return bfail(b, LBM_ERR_PARAM, "block_size must be 128 or 256");
     if (s.blocks_per_sm < 1 || s.blocks_per_sm > 8) return bfail(b, LBM_ERR_PARAM, "blocks_per_sm must be in [1, 8]");
     if (s.steps_per_launch < 1) return bfail(b, LBM_ERR_PARAM, "steps_per_launch must be >= 1");
+    if (s.tile_span < 1 || s.tile_span > 64) return bfail(b, LBM_ERR_PARAM, "tile_span must be in [1, 64]");
+    if (s.mode != 0 && s.mode != 1) return bfail(b, LBM_ERR_PARAM, "mode must be 0 or 1");
     if (s.graph_chunk < 0 || (s.graph_chunk > 0 && (s.graph_chunk % s.steps_per_launch || s.graph_chunk % 2)))
         return bfail(b, LBM_ERR_PARAM, "graph_chunk must be 0 or an even multiple of steps_per_launch");
     return LBM_OK;
@@ -1036,7 +1059,7 @@ lbm_status lbm_batch_create(lbm_ctx *const *cells, int ncells, void *stream, lbm
                                     b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_bar, 0, sizeof(GridBarrier), b->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-    lbm_status st = e == cudaSuccess ? build_tiles(b, b->sched.block_size)
+    lbm_status st = e == cudaSuccess ? build_tiles(b, b->sched.block_size, b->sched.tile_span)
                                      : bfail(b, LBM_ERR_CUDA, std::string("batch set-up: ") + cudaGetErrorString(e));
     if (st != LBM_OK) {
         lbm_batch_destroy(b);
@@ -1075,7 +1098,8 @@ lbm_status lbm_batch_set_schedule(lbm_batch *b, const lbm_schedule *s) {
     b->sched = *s;
     if (!b->stream) b->sched.graph_chunk = 0;
     drop_graph(b);
-    if (b->tiles_block != s->block_size) return build_tiles(b, s->block_size);
+    if (b->tiles_block != s->block_size || b->tiles_span != s->tile_span)
+        return build_tiles(b, s->block_size, s->tile_span);
     return LBM_OK;
 }
 
@@ -1097,6 +1121,11 @@ lbm_status lbm_batch_step(lbm_batch *b, int64_t n) {
     int grid = 0;
     lbm_status st = grid_for(b, b->sched, &grid);
     if (st != LBM_OK) return st;
+    if (b->sched.mode == 1)
+        for (int k = 0; k < 3; ++k)
+            if ((st = blocks_for_kernel(b, bstep_kernel_ptr(b->storage, k, b->sched.block_size), b->sched,
+                                        &b->grid_k[k])) != LBM_OK)
+                return st;
     int parity = p0;
     int64_t left = n;
     const int chunk = b->sched.graph_chunk, spl = b->sched.steps_per_launch;
@@ -1157,25 +1186,29 @@ lbm_status lbm_batch_autotune(lbm_batch *b, int trial_steps, lbm_schedule *best)
     BCK(b, cudaEventCreate(&e0));
     BCK(b, cudaEventCreate(&e1));
     const int blocks[2] = {128, 256};
+    const int spans[5] = {1, 2, 4, 8, 16};
     lbm_status st = LBM_OK;
+    for (int mode = 0; mode < 2 && st == LBM_OK; ++mode)
     for (int bi = 0; bi < 2 && st == LBM_OK; ++bi) {
-        for (int bps = 1; bps <= 3 && st == LBM_OK; ++bps) {
-            lbm_schedule s{blocks[bi], bps, keep.steps_per_launch, 0};
-            int occ = 0;
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batch_kernel_ptr(b->storage, s.block_size),
-                                                          s.block_size, 0);
-            if (bps > occ) continue;
-            if ((st = lbm_batch_set_schedule(b, &s)) != LBM_OK) break;
-            if ((st = lbm_batch_step(b, 2)) != LBM_OK) break; // warm-up
-            cudaEventRecord(e0, b->stream);
-            if ((st = lbm_batch_step(b, trial_steps)) != LBM_OK) break;
-            cudaEventRecord(e1, b->stream);
-            cudaEventSynchronize(e1);
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (ms < best_ms) {
-                best_ms = ms;
-                win = s;
+        int occ = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &occ, mode ? bstep_kernel_ptr(b->storage, TILE_EVEN, blocks[bi]) : batch_kernel_ptr(b->storage, blocks[bi]),
+            blocks[bi], 0);
+        for (int bps = 1; bps <= 4 && bps <= occ && st == LBM_OK; ++bps) {
+            for (int si = 0; si < 5 && st == LBM_OK; ++si) {
+                lbm_schedule s{blocks[bi], bps, keep.steps_per_launch, 0, spans[si], mode};
+                if ((st = lbm_batch_set_schedule(b, &s)) != LBM_OK) break;
+                if ((st = lbm_batch_step(b, 2)) != LBM_OK) break; // warm-up
+                cudaEventRecord(e0, b->stream);
+                if ((st = lbm_batch_step(b, trial_steps)) != LBM_OK) break;
+                cudaEventRecord(e1, b->stream);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    win = s;
+                }
             }
         }
     }

@@ -57,11 +57,18 @@ __host__ __device__ constexpr float w19(int i) {
 // -------------------------------------------------------- storage types ----
 
 enum StorageKind { ST_F32 = 0, ST_F16 = 1, ST_BF16 = 2, ST_F16M = 3 };
+// Element format of the FP16 thermal arrays: g times kGScale in FP16.  The
+// D3Q7 weights make the moving populations small (w_1 T ~ 1e-4 - 1e-2, and
+// far less where T ~ 0), and FP16 below 6.1e-5 is subnormal, with a fixed
+// spacing of 6e-8 and a biased stochastic rounding (see below); scaled by
+// 2^12 every |g| above 1.5e-8 is a normal number, and |g| up to 16 still fits.
+constexpr int ST_F16T = 4;
+constexpr float kGScale = 4096.f, kGUnscale = 1.f / 4096.f;
 
 // Element format of the flow (f) and thermal (g) arrays of a storage kind:
-// ST_F16M keeps f in FP16 and g in FP32.
+// ST_F16M keeps f in FP16 and g in FP32; ST_F16 keeps g in scaled FP16.
 __host__ __device__ constexpr int FS(int S) { return S == ST_F16M ? ST_F16 : S; }
-__host__ __device__ constexpr int GS(int S) { return S == ST_F16M ? ST_F32 : S; }
+__host__ __device__ constexpr int GS(int S) { return S == ST_F16M ? ST_F32 : S == ST_F16 ? ST_F16T : S; }
 
 // ------------------------------------------------- stochastic rounding ----
 //
@@ -92,7 +99,8 @@ __host__ __device__ __forceinline__ uint32_t rnd_pop(uint32_t r, int q) {
 // Stochastic rounding of an FP32 value to FP16 / BF16: add random bits below
 // the kept significand to the magnitude, then truncate towards zero (exact
 // for normal numbers; below the FP16 normal range, 6.1e-5, the result can be
-// biased towards zero by less than one FP16 subnormal spacing, 6e-8).
+// biased towards zero by up to one FP16 subnormal spacing, 6e-8, which is
+// why the thermal populations are stored scaled, ST_F16T).
 __device__ __forceinline__ float sr_pre16(float v, uint32_t r) {
     return __uint_as_float(__float_as_uint(v) + (r >> 19));
 }
@@ -127,6 +135,14 @@ template <> struct Store<ST_F16> {
         *p = __float2half_rz(sr_pre16(v, r));
     }
 };
+template <> struct Store<ST_F16T> {
+    using T = __half;
+    static __device__ __forceinline__ float ld(const __half *p) { return __half2float(*p) * kGUnscale; }
+    static __device__ __forceinline__ void st(__half *p, float v) { *p = __float2half_rn(v * kGScale); }
+    static __device__ __forceinline__ void sts(__half *p, float v, uint32_t r) {
+        *p = __float2half_rz(sr_pre16(v * kGScale, r));
+    }
+};
 template <> struct Store<ST_BF16> {
     using T = __nv_bfloat16;
     static __device__ __forceinline__ float ld(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
@@ -152,6 +168,18 @@ template <> struct Store2<ST_F16> {
     }
     static __device__ __forceinline__ void sts(__half *p, float2 v, uint32_t r0, uint32_t r1) {
         *reinterpret_cast<__half2 *>(p) = h2_sr(v, r0, r1);
+    }
+};
+template <> struct Store2<ST_F16T> {
+    static __device__ __forceinline__ float2 ld(const __half *p) {
+        const float2 v = __half22float2(*reinterpret_cast<const __half2 *>(p));
+        return make_float2(v.x * kGUnscale, v.y * kGUnscale);
+    }
+    static __device__ __forceinline__ void st(__half *p, float2 v) {
+        *reinterpret_cast<__half2 *>(p) = __float22half2_rn(make_float2(v.x * kGScale, v.y * kGScale));
+    }
+    static __device__ __forceinline__ void sts(__half *p, float2 v, uint32_t r0, uint32_t r1) {
+        *reinterpret_cast<__half2 *>(p) = h2_sr(make_float2(v.x * kGScale, v.y * kGScale), r0, r1);
     }
 };
 template <> struct Store2<ST_BF16> {

@@ -108,7 +108,7 @@ __device__ __forceinline__ float dval(float pm, float p0, float pp, bool wm, boo
 // nodes; the rare wall terms go into shared FP64 sums.
 constexpr int kDiagTX = 32, kDiagTY = kDiagThreads / kDiagTX, kDiagSeg = 32;
 
-__global__ void __launch_bounds__(kDiagThreads) k_diag(const float *__restrict__ mom, Geom G, Phys P,
+__global__ void __launch_bounds__(kDiagThreads, 3) k_diag(const float *__restrict__ mom, Geom G, Phys P,
                                                        WallT W, double *__restrict__ partial) {
     __shared__ double sh[kDiagThreads / 32][kNDiag];
     __shared__ float pl[4][kDiagTY + 2][kDiagTX + 2]; // u, v, w, T of the current plane, with halo
@@ -134,39 +134,59 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag(const float *__restrict__
         const bool col = x < nx && y < ny;
         const int z0 = kb * kDiagSeg, z1 = min(nz, z0 + kDiagSeg);
         const uint32_t c = (uint32_t)(col ? x : 0) + (uint32_t)nx * (uint32_t)(col ? y : 0); // column offset
-        // registers: the column's fields at z - 1 (pm), z (p0), z + 1 (pp)
-        float pm[4], p0[4], pp[4];
+        // halo cells this thread loads: row y - 1 or y + kDiagTY (hy), column
+        // x - 1 or x + kDiagTX (hx), as flat in-plane offsets, -1 where none
+        int64_t hy = -1, hx = -1;
+        if (ty == 0 || ty == kDiagTY - 1) {
+            const int yh = ty == 0 ? jb * kDiagTY - 1 : jb * kDiagTY + kDiagTY;
+            const int yw = yh < 0 ? (pery ? ny - 1 : -1) : yh >= ny ? (pery ? yh - ny : -1) : yh;
+            if (yw >= 0 && x < nx) hy = (int64_t)x + (int64_t)nx * yw;
+        }
+        if (tx == 0 || tx == kDiagTX - 1) {
+            const int xh = tx == 0 ? ib * kDiagTX - 1 : ib * kDiagTX + kDiagTX;
+            const int xw = xh < 0 ? (perx ? nx - 1 : -1) : xh >= nx ? (perx ? xh - nx : -1) : xh;
+            if (xw >= 0 && y < ny) hx = (int64_t)xw + (int64_t)nx * y;
+        }
+        const int ry = ty == 0 ? 0 : kDiagTY + 1, cx = tx == 0 ? 0 : kDiagTX + 1;
+        auto zwrap = [&](int zz) { return zz < nz ? zz : (perz ? zz - nz : nz - 1); };
+        // registers: the column's fields at z - 1 (pm), z (p0), z + 1 (pp), and the
+        // loads for the next plane in flight: z + 2 (pn), the halo of z + 1, rho of z + 1
+        float pm[4], p0[4], pp[4], pn[4], hyv[4], hxv[4];
+        float d0;
         const int zb = z0 > 0 ? z0 - 1 : (perz ? nz - 1 : 0);
+        {
+            const uint32_t pb = G.nxy * (uint32_t)zb, p0z = G.nxy * (uint32_t)z0, p1 = G.nxy * (uint32_t)zwrap(z0 + 1);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            pm[q] = col ? F[q][c + G.nxy * (uint32_t)zb] : 0.f;
-            p0[q] = col ? F[q][c + G.nxy * (uint32_t)z0] : 0.f;
+            for (int q = 0; q < 4; ++q) {
+                pm[q] = col ? F[q][c + pb] : 0.f;
+                p0[q] = col ? F[q][c + p0z] : 0.f;
+                pp[q] = col ? F[q][c + p1] : 0.f;
+                hyv[q] = hy >= 0 ? F[q][hy + p0z] : 0.f;
+                hxv[q] = hx >= 0 ? F[q][hx + p0z] : 0.f;
+            }
+            d0 = col ? dr[c + p0z] : 0.f;
         }
         for (int z = z0; z < z1; ++z) {
             const bool zlo = z == 0 && !perz, zhi = z == nz - 1 && !perz;
-            const int zn = z + 1 < nz ? z + 1 : (perz ? 0 : z);
             const uint32_t plane = G.nxy * (uint32_t)z;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) pp[q] = col ? F[q][c + G.nxy * (uint32_t)zn] : 0.f;
             // the current plane into shared memory: own values, then the halo
 #pragma unroll
-            for (int q = 0; q < 4; ++q) pl[q][ty + 1][tx + 1] = p0[q];
-            if (ty == 0 || ty == kDiagTY - 1) { // rows y - 1 and y + kDiagTY (wrapped when y is periodic)
-                const int yh = ty == 0 ? jb * kDiagTY - 1 : jb * kDiagTY + kDiagTY;
-                const int yw = yh < 0 ? (pery ? ny - 1 : -1) : yh >= ny ? (pery ? yh - ny : -1) : yh;
-                const int r = ty == 0 ? 0 : kDiagTY + 1;
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    pl[q][r][tx + 1] = (yw >= 0 && x < nx) ? F[q][(uint32_t)x + (uint32_t)nx * (uint32_t)yw + plane] : 0.f;
+            for (int q = 0; q < 4; ++q) {
+                pl[q][ty + 1][tx + 1] = p0[q];
+                if (ty == 0 || ty == kDiagTY - 1) pl[q][ry][tx + 1] = hyv[q];
+                if (tx == 0 || tx == kDiagTX - 1) pl[q][ty + 1][cx] = hxv[q];
             }
-            if (tx == 0 || tx == kDiagTX - 1) { // columns x - 1 and x + kDiagTX
-                const int xh = tx == 0 ? ib * kDiagTX - 1 : ib * kDiagTX + kDiagTX;
-                const int xw = xh < 0 ? (perx ? nx - 1 : -1) : xh >= nx ? (perx ? xh - nx : -1) : xh;
-                const int cc = tx == 0 ? 0 : kDiagTX + 1;
+            // issue the next plane's loads now; they complete during this plane's work
+            const bool more = z + 1 < z1;
+            const uint32_t nplane = G.nxy * (uint32_t)zwrap(z + 1), n2 = G.nxy * (uint32_t)zwrap(z + 2);
+            float dn = 0.f;
 #pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    pl[q][ty + 1][cc] = (xw >= 0 && y < ny) ? F[q][(uint32_t)xw + (uint32_t)nx * (uint32_t)y + plane] : 0.f;
+            for (int q = 0; q < 4; ++q) {
+                pn[q] = (more && col) ? F[q][c + n2] : 0.f;
+                hyv[q] = (more && hy >= 0) ? F[q][hy + nplane] : 0.f;
+                hxv[q] = (more && hx >= 0) ? F[q][hx + nplane] : 0.f;
             }
+            if (more && col) dn = dr[c + nplane];
             __syncthreads();
             if (col) {
                 const uint32_t n = c + plane;
@@ -194,7 +214,7 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag(const float *__restrict__
                         gT[2] = dval(pm[3], p0[3], pp[3], zlo, zhi, dir[4], W.Tw[4], dir[5], W.Tw[5]);
                     }
                 }
-                const float d = dr[n], u = p0[0], vv = p0[1], w = p0[2], t = p0[3];
+                const float d = d0, u = p0[0], vv = p0[1], w = p0[2], t = p0[3];
                 const float uu = u * u + vv * vv + w * w;
                 float eps = 0.f;
 #pragma unroll
@@ -237,7 +257,9 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag(const float *__restrict__
             for (int q = 0; q < 4; ++q) {
                 pm[q] = p0[q];
                 p0[q] = pp[q];
+                pp[q] = pn[q];
             }
+            d0 = dn;
         }
     }
     double v[kNDiag];

@@ -20,6 +20,7 @@ struct StagedGeom {
     uint32_t tpp;        // odd-step tiles per z-plane
     uint64_t mag_tpp;    // division magic of tpp
     int grid;            // persistent blocks
+    int xf;              // 1: the odd kernel updates the x-face nodes of its rows (nx >= staged_xf_min_nx())
     long long budget;    // clock cycles one pipeline wait may take
 };
 
@@ -53,6 +54,7 @@ cudaError_t launch_staged(const StepArgs &a);
 cudaError_t staged_prepare(int storage, int *blocks_per_sm);
 int staged_smem_bytes(int storage);
 int staged_tile_nodes();
+int staged_xf_min_nx();
 // op 0: staging -> device layout, 1: device layout -> staging, 2: moments -> st
 cudaError_t launch_convert(int storage, int op, float *st, void *f, void *g, const Geom &G,
                            const Phys &P, int layout, cudaStream_t stream);
@@ -97,7 +99,8 @@ struct CellDev {
 enum TileKind { TILE_EVEN = 0, TILE_ROWS = 1, TILE_FACE = 2 };
 struct Tile {
     int cell, kind;
-    uint32_t blk; // block index of the single-cell kernel this tile stands for
+    uint32_t blk;  // first block index of the single-cell kernel this tile stands for
+    uint32_t nblk; // consecutive blocks it covers
 };
 struct GridBarrier {
     unsigned count, gen;
@@ -106,15 +109,19 @@ struct GridBarrier {
 };
 struct BatchArgs {
     const CellDev *cells;
-    const Tile *even, *odd;
-    int n_even, n_odd, nsteps, parity0;
+    const Tile *even, *odd;         // odd = row tiles followed by face tiles
+    const Tile *rows, *faces;
+    int n_even, n_odd, n_rows, n_faces, nsteps, parity0;
     GridBarrier *bar;
     long long budget;
+    int mode;                       // 0: cooperative multi-step launch, 1: one launch per step and tile kind
     int grid, block;
+    int grid_k[3];                  // mode 1: grid of each tile kind's kernel
     cudaStream_t stream;
 };
 // block is 128 or 256 threads (two compiled variants)
 const void *batch_kernel_ptr(int storage, int block);
+const void *bstep_kernel_ptr(int storage, int kind, int block);
 cudaError_t launch_batch(int storage, const BatchArgs &a);
 
 // Loads, on the current device, the static scratch of lbm_reduce_noalloc

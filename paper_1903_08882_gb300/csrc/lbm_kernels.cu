@@ -361,8 +361,9 @@ __global__ void __launch_bounds__(256, 2) k_aa_odd_rows(SEF<S> *__restrict__ f, 
 // ------------------------------------------------- batched persistent launch ----
 //
 // Many independent cells advance in one launch.  The cells' tiles (a tile is
-// one block's share of one cell's step: a 512-node pair range of the even
-// step, a 512-node row chunk of the odd step, or a range of face nodes) are
+// a run of consecutive blocks of one cell's single-cell kernels: 512-node
+// pair ranges of the even step, 512-node row chunks of the odd step, or
+// ranges of face nodes; the run length is the schedule's tile span) are
 // listed per step parity; the blocks of a persistent grid stride over the
 // list and meet at a grid-wide barrier after every time step.  The launch is
 // cooperative, so all blocks are resident; the barrier still gives up after
@@ -393,16 +394,74 @@ __global__ void __launch_bounds__(BS, BS == 128 ? 3 : 2)
             __syncthreads();
             SEF<S> *f = static_cast<SEF<S> *>(sc.f);
             SEG<S> *g = static_cast<SEG<S> *>(sc.g);
-            if (st.kind == TILE_EVEN)
-                k_aa_even2_tile<S, false>(f, g, sc.G, sc.P, nullptr, st.blk, threadIdx.x, BS);
-            else if (st.kind == TILE_ROWS)
-                k_aa_odd_rows_tile<S, false>(f, g, sc.G, sc.P, nullptr, st.blk, threadIdx.x, BS);
-            else
-                k_aa_odd_face_tile<S, false>(f, g, sc.G, sc.P, nullptr, sc.face, sc.nface, st.blk, threadIdx.x, BS);
+            for (uint32_t k = 0; k < st.nblk; ++k) {
+                const uint32_t blk = st.blk + k;
+                if (st.kind == TILE_EVEN)
+                    k_aa_even2_tile<S, false>(f, g, sc.G, sc.P, nullptr, blk, threadIdx.x, BS);
+                else if (st.kind == TILE_ROWS)
+                    k_aa_odd_rows_tile<S, false>(f, g, sc.G, sc.P, nullptr, blk, threadIdx.x, BS);
+                else
+                    k_aa_odd_face_tile<S, false>(f, g, sc.G, sc.P, nullptr, sc.face, sc.nface, blk, threadIdx.x, BS);
+            }
         }
         if (!grid_barrier(bar, gridDim.x, budget)) return;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) bar->steps = t0 + (uint32_t)nsteps;
+}
+
+// Per-step mode: one launch per time step and tile kind (even tiles; or row
+// tiles, then face tiles), each a persistent grid striding over that kind's
+// tiles.  The launch boundaries order the steps, so there is no grid barrier,
+// and each kind gets its own register allocation (the three tile bodies in
+// one kernel need 168 registers per thread, each alone at most 128).  k_bump
+// advances the batch's step counter after each step.
+template <int S, int KIND, int BS>
+__global__ void __launch_bounds__(BS, BS == 128 ? 4 : 2)
+    k_bstep(const CellDev *__restrict__ cells, const Tile *__restrict__ tl, int nt, const GridBarrier *bar) {
+    __shared__ CellDev sc;
+    __shared__ Tile st;
+    const uint32_t t0 = *reinterpret_cast<const volatile unsigned *>(&bar->steps);
+    for (int t = blockIdx.x; t < nt; t += gridDim.x) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            st = tl[t];
+            sc = cells[st.cell];
+            sc.P.t += t0;
+        }
+        __syncthreads();
+        SEF<S> *f = static_cast<SEF<S> *>(sc.f);
+        SEG<S> *g = static_cast<SEG<S> *>(sc.g);
+        for (uint32_t k = 0; k < st.nblk; ++k) {
+            const uint32_t blk = st.blk + k;
+            if (KIND == TILE_EVEN)
+                k_aa_even2_tile<S, false>(f, g, sc.G, sc.P, nullptr, blk, threadIdx.x, BS);
+            else if (KIND == TILE_ROWS)
+                k_aa_odd_rows_tile<S, false>(f, g, sc.G, sc.P, nullptr, blk, threadIdx.x, BS);
+            else
+                k_aa_odd_face_tile<S, false>(f, g, sc.G, sc.P, nullptr, sc.face, sc.nface, blk, threadIdx.x, BS);
+        }
+    }
+}
+
+__global__ void k_bump(GridBarrier *bar) { bar->steps += 1u; }
+
+template <int S> static const void *bstep_kernel(int kind, int block) {
+    if (block == 128)
+        return kind == TILE_EVEN ? reinterpret_cast<const void *>(&k_bstep<S, TILE_EVEN, 128>)
+             : kind == TILE_ROWS ? reinterpret_cast<const void *>(&k_bstep<S, TILE_ROWS, 128>)
+                                 : reinterpret_cast<const void *>(&k_bstep<S, TILE_FACE, 128>);
+    return kind == TILE_EVEN ? reinterpret_cast<const void *>(&k_bstep<S, TILE_EVEN, 256>)
+         : kind == TILE_ROWS ? reinterpret_cast<const void *>(&k_bstep<S, TILE_ROWS, 256>)
+                             : reinterpret_cast<const void *>(&k_bstep<S, TILE_FACE, 256>);
+}
+
+const void *bstep_kernel_ptr(int storage, int kind, int block) {
+    switch (storage) {
+    case ST_F32: return bstep_kernel<ST_F32>(kind, block);
+    case ST_F16: return bstep_kernel<ST_F16>(kind, block);
+    case ST_F16M: return bstep_kernel<ST_F16M>(kind, block);
+    default: return bstep_kernel<ST_BF16>(kind, block);
+    }
 }
 
 template <int S> static const void *batch_kernel(int block) {
@@ -420,6 +479,27 @@ const void *batch_kernel_ptr(int storage, int block) {
 }
 
 cudaError_t launch_batch(int storage, const BatchArgs &a) {
+    if (a.mode == 1) {
+        for (int k = 0; k < a.nsteps; ++k) {
+            const bool odd_step = ((a.parity0 + k) & 1) != 0;
+            const int kinds[2] = {odd_step ? TILE_ROWS : TILE_EVEN, odd_step ? TILE_FACE : -1};
+            for (int kind : kinds) {
+                if (kind < 0) continue;
+                const Tile *tl = kind == TILE_EVEN ? a.even : kind == TILE_ROWS ? a.rows : a.faces;
+                int nt = kind == TILE_EVEN ? a.n_even : kind == TILE_ROWS ? a.n_rows : a.n_faces;
+                if (nt == 0) continue;
+                const GridBarrier *bar = a.bar;
+                void *args[] = {(void *)&a.cells, (void *)&tl, (void *)&nt, (void *)&bar};
+                const cudaError_t e = cudaLaunchKernel(bstep_kernel_ptr(storage, kind, a.block), dim3(a.grid_k[kind]),
+                                                       dim3(a.block), args, 0, a.stream);
+                if (e != cudaSuccess) return e;
+            }
+            k_bump<<<1, 1, 0, a.stream>>>(a.bar);
+            const cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
     void *args[] = {(void *)&a.cells, (void *)&a.even, (void *)&a.n_even, (void *)&a.odd, (void *)&a.n_odd,
                     (void *)&a.nsteps, (void *)&a.parity0, (void *)&a.bar, (void *)&a.budget};
     cudaLaunchConfig_t cfg = {};

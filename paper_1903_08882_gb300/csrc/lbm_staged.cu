@@ -20,22 +20,21 @@
 // Even step: every node, natural -> reversed layout (own slots only); a
 // thread takes two adjacent nodes and moves each population pair with one
 // vector access.
-// Odd step: the nodes 1 <= x <= nx-2 of the rows 1 <= y <= ny-2 of the
-// planes 1 <= z <= nz-2; a warp takes 64 consecutive nodes, lane l the nodes
-// l and l + 32, so that its stores to the shifted destinations stay
-// contiguous.  Every node next to a face goes to the general face kernel.
-// (Four ways of updating the x-face nodes here measured slower at 257^3
-// than leaving them to the face kernel, 494 us per FP16 odd step: their wall
-// links loaded per lane before the wait (740 us), fetched as 16-byte bulk
-// copies into the stage (617 us: the copy engine takes tiny copies one by
-// one), fetched by per-thread 4-byte asynchronous copies completing on the
-// stage's barrier (510 us: the extra flags and addresses push the kernel past
-// its 128 registers into local memory), or listed and updated by one warp
-// every few tiles (549 us: that warp waits on L2 while the block waits for it
-// at the next barrier).  Scheduling the face kernel's x-face work as items of
-// this kernel, right after the tiles whose windows hold their neighbourhood,
-// gave 490 us: the cost is the general path on strided nodes, not DRAM
-// re-reads.)
+// Odd step: the rows 1 <= y <= ny-2 of the planes 1 <= z <= nz-2; a warp
+// takes 64 consecutive nodes, lane l the nodes l and l + 32, so that its
+// stores to the shifted destinations stay contiguous.  For rows of at least
+// kXfMinNx nodes the nodes at x = 0 and x = nx-1 of those rows are updated
+// here too: the six values that arrive through the x face (bounce-back from
+// the node's own slot, or the far end of the row when x is periodic) are not
+// in the shifted windows, so the issuing warp fetches each as one 4-byte
+// asynchronous copy (cp.async) into the stage, completing on the stage's
+// barrier, and the links that leave through the face are stored to the
+// node's own slots.  The nodes next to a y or z face (and, for shorter rows,
+// the x-face nodes) go to the general face kernel.  (Leaving the x-face nodes
+// to the face kernel costs it strided 32-byte sectors, 594 B read per node
+// against 52 B algorithmic; in-tile they cost 5% of the odd step less at
+// 257^3.  A variant that handed stages over through per-warp mbarriers
+// instead of a block barrier per tile measured 3-6% slower.)
 // Every location a node reads is written by that node only, so the in-place
 // update is race-free whatever order the tiles run in.
 #include "lbm_device.cuh"
@@ -53,11 +52,18 @@ constexpr int kTile = 2 * kThreads;     // nodes per tile
 constexpr int kSlack = 32;              // window bytes beyond the tile: 16-byte rounding at both ends
 constexpr int kHead = 1024;             // shared-memory header: mbarriers and window shifts
 constexpr long long kDrain = 1ll << 31; // cycles to wait for copies in flight before leaving after a timeout
+// In-tile x faces: a tile of kTile consecutive nodes touches at most
+// kXfRows rows of at least kXfMinNx nodes; each row has two x-face nodes and
+// each of them 5 + 1 links through its face.
+constexpr int kXfMinNx = 16;
+constexpr int kXfRows = (kTile - 1) / kXfMinNx + 2;
+constexpr int kSide = kXfRows * 2 * 6 * 4; // one 4-byte word per x-face link
 
 template <int S> struct Stage {
     static constexpr int fwin = kTile * (int)sizeof(SF<S>) + kSlack;
     static constexpr int gwin = kTile * (int)sizeof(SG<S>) + kSlack;
-    static constexpr int bytes = 19 * fwin + 7 * gwin;
+    static constexpr int win = 19 * fwin + 7 * gwin; // the 26 windows, then the x-face words
+    static constexpr int bytes = win + kSide;
     static constexpr int count = (sizeof(SF<S>) == 4) ? 2 : 3; // stages in flight per block
     static constexpr int smem = kHead + count * bytes;
     static __device__ __forceinline__ int offset(int q) { return q < 19 ? q * fwin : 19 * fwin + (q - 19) * gwin; }
@@ -106,51 +112,41 @@ __device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned b
                  : "memory");
 }
 
+// 4-byte asynchronous copy global -> shared (both addresses 4-byte aligned).
+__device__ __forceinline__ void word_load(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sptr(dst)), "l"(src) : "memory");
+}
+// One arrival on `bar` once this thread's earlier cp.async copies have landed
+// (counted in the barrier's expected arrivals).
+__device__ __forceinline__ void word_arrive(uint64_t *bar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(sptr(bar)) : "memory");
+}
+
 // ------------------------------------------------- element helpers ----
-
-__device__ __forceinline__ float tof(float v) { return v; }
-__device__ __forceinline__ float tof(__half v) { return __half2float(v); }
-__device__ __forceinline__ float tof(__nv_bfloat16 v) { return __bfloat162float(v); }
-
-template <typename E> struct Pair;
-// st / st1: round to nearest; sts / st1s: stochastic rounding with the
-// random bits r (the thermal populations of the 2-byte storages, see
-// lbm_device.cuh).
-template <> struct Pair<float> {
-    static __device__ __forceinline__ float2 ld(const float *p) { return *reinterpret_cast<const float2 *>(p); }
-    static __device__ __forceinline__ void st(float *p, float2 v) { *reinterpret_cast<float2 *>(p) = v; }
-    static __device__ __forceinline__ void st1(float *p, float v) { *p = v; }
-    static __device__ __forceinline__ void sts(float *p, float2 v, uint32_t, uint32_t) { st(p, v); }
-    static __device__ __forceinline__ void st1s(float *p, float v, uint32_t) { *p = v; }
+//
+// Per storage format FMT (lbm_device.cuh): one: an element to FP32;
+// word: the element with index parity `odd` of the aligned 4-byte word
+// holding it; ld: two consecutive elements (first index even); st / st1:
+// round to nearest; sts / st1s: the thermal populations' stochastic rounding
+// with random bits r.
+template <int FMT> struct PairF {
+    using E = typename Store<FMT>::T;
+    static __device__ __forceinline__ float one(E v) { return Store<FMT>::ld(&v); }
+    static __device__ __forceinline__ float word(uint32_t w, uint32_t odd) {
+        if (sizeof(E) == 4) return Store<FMT>::ld(reinterpret_cast<const E *>(&w));
+        const unsigned short h = (unsigned short)(odd ? w >> 16 : w & 0xffffu);
+        return Store<FMT>::ld(reinterpret_cast<const E *>(&h));
+    }
+    static __device__ __forceinline__ float2 ld(const E *p) { return Store2<FMT>::ld(p); }
+    static __device__ __forceinline__ void st(E *p, float2 v) { Store2<FMT>::st(p, v); }
+    static __device__ __forceinline__ void st1(E *p, float v) { Store<FMT>::st(p, v); }
+    static __device__ __forceinline__ void sts(E *p, float2 v, uint32_t r0, uint32_t r1) {
+        Store2<FMT>::sts(p, v, r0, r1);
+    }
+    static __device__ __forceinline__ void st1s(E *p, float v, uint32_t r) { Store<FMT>::sts(p, v, r); }
 };
-template <> struct Pair<__half> {
-    static __device__ __forceinline__ float2 ld(const __half *p) {
-        return __half22float2(*reinterpret_cast<const __half2 *>(p));
-    }
-    static __device__ __forceinline__ void st(__half *p, float2 v) {
-        *reinterpret_cast<__half2 *>(p) = __float22half2_rn(v);
-    }
-    static __device__ __forceinline__ void st1(__half *p, float v) { *p = __float2half_rn(v); }
-    static __device__ __forceinline__ void sts(__half *p, float2 v, uint32_t r0, uint32_t r1) {
-        *reinterpret_cast<__half2 *>(p) = h2_sr(v, r0, r1);
-    }
-    static __device__ __forceinline__ void st1s(__half *p, float v, uint32_t r) { *p = __float2half_rz(sr_pre16(v, r)); }
-};
-template <> struct Pair<__nv_bfloat16> {
-    static __device__ __forceinline__ float2 ld(const __nv_bfloat16 *p) {
-        return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p));
-    }
-    static __device__ __forceinline__ void st(__nv_bfloat16 *p, float2 v) {
-        *reinterpret_cast<__nv_bfloat162 *>(p) = __float22bfloat162_rn(v);
-    }
-    static __device__ __forceinline__ void st1(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
-    static __device__ __forceinline__ void sts(__nv_bfloat16 *p, float2 v, uint32_t r0, uint32_t r1) {
-        *reinterpret_cast<__nv_bfloat162 *>(p) = bf2_sr(v, r0, r1);
-    }
-    static __device__ __forceinline__ void st1s(__nv_bfloat16 *p, float v, uint32_t r) {
-        *p = __float2bfloat16_rz(sr_pre_bf(v, r));
-    }
-};
+template <int S> using PF = PairF<FS(S)>; // flow arrays
+template <int S> using PG = PairF<GS(S)>; // thermal arrays
 
 // Flat offset of e_i for population q (0..18 flow, 19..25 thermal: the D3Q7
 // velocities e_0..e_6 equal the D3Q19 ones).
@@ -163,6 +159,9 @@ __host__ __device__ __forceinline__ int opp_idx(int i) {
 }
 // Array an odd step reads population q from: the opposite slot.
 __host__ __device__ __forceinline__ int src_array(int q) { return q < 19 ? opp_idx(q) : 19 + opp_idx(q - 19); }
+
+// D3Q19 links with e_x = +1 (side 0) or -1 (side 1), j = 0..4: 1 7 9 11 13 / 2 8 10 12 14.
+__host__ __device__ constexpr int xlink(int side, int j) { return (j == 0 ? 1 : 5 + 2 * j) + side; }
 
 // Tile t of a step: its first node and the node range it updates.
 struct TileSpan {
@@ -184,19 +183,27 @@ template <bool ODD> __device__ __forceinline__ TileSpan tile_span(const Geom &G,
     return s;
 }
 
-// Copy the 26 windows of a tile into one stage.  Called by all 32 lanes of
-// one warp: lane q < 26 computes and issues window q.  shift[q] receives
+// Copy one tile into a stage.  Called by all 32 lanes of one warp.
+// Lane q < 26 computes and issues window q: shift[q] receives
 // n0 - off_q - (first element copied), so that node n0 + j of the tile sits
 // at element j + shift[q] of window q.
-template <int S, bool ODD>
-__device__ __forceinline__ void issue_tile(const SF<S> *f, const SG<S> *g, const Geom &G, uint32_t n0,
+// XF (odd step, rows of at least kXfMinNx nodes): the values that arrive at
+// the tile's x-face nodes through their face are not in the windows (they
+// come from the node's own slot at a wall, or from the far end of the row
+// when x is periodic); the lanes fetch each one as the aligned 4-byte word
+// holding it into the stage's x-face area, word (2 R + side) 6 + j for the
+// face node of the tile's R-th row on side 0 (x = 0) or 1 (x = nx-1) and
+// its link j (five flow links, then the thermal one), completion counted on
+// the same barrier.
+template <int S, bool ODD, bool XF>
+__device__ __forceinline__ void issue_tile(const SF<S> *f, const SG<S> *g, const Geom &G, const TileSpan &sp,
                                            unsigned char *stage, int *shift, uint64_t *bar, int lane) {
     unsigned sz = 0;
     const char *src = nullptr;
     if (lane < 26) {
         const int q = lane;
         const int64_t es = q < 19 ? (int64_t)sizeof(SF<S>) : (int64_t)sizeof(SG<S>);
-        const int64_t first = (int64_t)n0 - (ODD ? pop_off(G, q) : 0);
+        const int64_t first = (int64_t)sp.n0 - (ODD ? pop_off(G, q) : 0);
         int64_t a = (first * es) & ~(int64_t)15;
         int64_t b = ((first + kTile) * es + 15) & ~(int64_t)15;
         const int64_t lim = G.stride * es;
@@ -214,9 +221,84 @@ __device__ __forceinline__ void issue_tile(const SF<S> *f, const SG<S> *g, const
     if (lane == 0) mbar_expect_tx(bar, total);
     __syncwarp();
     if (sz) bulk_load(stage + Stage<S>::offset(lane), src, sz, bar);
+    if (XF) {
+        uint32_t *side = reinterpret_cast<uint32_t *>(stage + Stage<S>::win);
+        const uint32_t nx = (uint32_t)G.nx;
+        const uint32_t row0 = fast_div(sp.n0, G.mag_nx);
+        const uint32_t rows = fast_div(sp.n0 + (uint32_t)kTile - 1u, G.mag_nx) - row0 + 1u;
+        const uint32_t beg = sp.n0 > sp.lo ? sp.n0 : sp.lo;
+        const uint32_t end = sp.n0 + (uint32_t)kTile < sp.hi ? sp.n0 + (uint32_t)kTile : sp.hi;
+        const bool per = G.periodic & 1;
+        const int64_t s = G.stride;
+        for (uint32_t k = (uint32_t)lane; k < rows * 12u; k += 32u) {
+            const uint32_t R = k / 12u, rem = k - 12u * R, sd = rem / 6u, j = rem - 6u * sd;
+            const uint32_t n = (row0 + R) * nx + (sd ? nx - 1u : 0u);
+            if (n < beg || n >= end) continue;
+            const int q = j < 5u ? xlink((int)sd, (int)j) : 1 + (int)sd; // flow / thermal link index
+            // wall: the node's own slot q; periodic: slot qbar of n - e_q wrapped along the row
+            const int64_t at = per ? (int64_t)n - G.off[q] + (sd ? -(int64_t)nx : (int64_t)nx) : (int64_t)n;
+            const int arr = per ? opp_idx(q) : q;
+            const char *p = j < 5u ? reinterpret_cast<const char *>(f + (int64_t)arr * s + at)
+                                   : reinterpret_cast<const char *>(g + (int64_t)arr * s + at);
+            word_load(side + k, reinterpret_cast<const void *>(reinterpret_cast<uintptr_t>(p) & ~(uintptr_t)3));
+        }
+        word_arrive(bar);
+    }
 }
 
-template <int S, bool ODD>
+// x-face node (side 0: x = 0, side 1: x = nx-1) of component K of a pair:
+// the links that arrive through its face take the fetched words (w: the
+// node's six words), with anti-bounce-back for g at a Dirichlet face.
+template <int S, int SIDE, int K>
+__device__ __forceinline__ void xface_in(float2 (&fl)[19], float2 (&gl)[7], const uint32_t *w, uint32_t n,
+                                         const Geom &G, const Phys &P) {
+    const bool per = G.periodic & 1;
+    const int64_t wrap = SIDE ? -(int64_t)G.nx : (int64_t)G.nx;
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+        const int q = xlink(SIDE, j);
+        const uint32_t at = per ? (uint32_t)((int64_t)n - G.off[q] + wrap) : n;
+        const float v = PF<S>::word(w[j], at & 1u);
+        if (K == 0) fl[q].x = v;
+        else fl[q].y = v;
+    }
+    const int q = 1 + SIDE;
+    const uint32_t at = per ? (uint32_t)((int64_t)n - G.off[q] + wrap) : n;
+    float v = PG<S>::word(w[5], at & 1u);
+    if (!per && ((P.dir_mask >> SIDE) & 1)) v = P.abbT[SIDE] - v; // the link comes through face SIDE
+    if (K == 0) gl[q].x = v;
+    else gl[q].y = v;
+}
+
+// The links that leave an x-face node through its face: bounce-back into the
+// node's own opposite slot (anti-bounce-back for g at a Dirichlet face), or
+// the far end of the row when x is periodic.
+template <int S, int SIDE, int K>
+__device__ __forceinline__ void xface_out(SF<S> *f, SG<S> *g, const float2 (&fl)[19], const float2 (&gl)[7],
+                                          uint32_t n, uint32_t rb, const Geom &G, const Phys &P) {
+    const bool per = G.periodic & 1;
+    const int64_t s = G.stride;
+    const int64_t wrap = SIDE ? (int64_t)G.nx : -(int64_t)G.nx; // side 0 leaves along -x
+#pragma unroll
+    for (int j = 0; j < 5; ++j) {
+        const int q = xlink(1 - SIDE, j); // e_x = -1 at x = 0, +1 at x = nx-1
+        const float v = K == 0 ? fl[q].x : fl[q].y;
+        SF<S> *p = per ? f + q * s + ((int64_t)n + G.off[q] - wrap) : f + opp19(q) * s + n;
+        PF<S>::st1(p, v);
+    }
+    const int q = 2 - SIDE;
+    float v = K == 0 ? gl[q].x : gl[q].y;
+    SG<S> *p;
+    if (per) {
+        p = g + q * s + ((int64_t)n + G.off[q] - wrap);
+    } else {
+        p = g + opp7(q) * s + n;
+        if ((P.dir_mask >> SIDE) & 1) v = P.abbT[SIDE] - v; // the link leaves through face SIDE
+    }
+    PG<S>::st1s(p, v, rnd_pop(rb, q));
+}
+
+template <int S, bool ODD, bool XF>
 __global__ void __launch_bounds__(kThreads, 2)
     k_aa_staged(SF<S> *__restrict__ f, SG<S> *__restrict__ g, Geom G, Phys P, StagedGeom T, int *err) {
     constexpr int NST = Stage<S>::count;
@@ -230,7 +312,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     const int64_t s = G.stride;
 
     if (tid == 0) {
-        for (int k = 0; k < NST; ++k) mbar_init(&bar[k], 1);
+        for (int k = 0; k < NST; ++k) mbar_init(&bar[k], XF ? 33u : 1u); // + one per lane's word copies
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -239,8 +321,8 @@ __global__ void __launch_bounds__(kThreads, 2)
         for (int k = 0; k < NST; ++k) {
             const uint32_t t = blockIdx.x + (uint32_t)k * gridDim.x;
             if (t < ntiles)
-                issue_tile<S, ODD>(f, g, G, tile_span<ODD>(G, T, t).n0, stages + k * Stage<S>::bytes,
-                                   shift + 26 * k, &bar[k], lane);
+                issue_tile<S, ODD, XF>(f, g, G, tile_span<ODD>(G, T, t), stages + k * Stage<S>::bytes,
+                                       shift + 26 * k, &bar[k], lane);
         }
     }
 
@@ -255,11 +337,22 @@ __global__ void __launch_bounds__(kThreads, 2)
         const uint32_t mb = m + (ODD ? 32u : 1u);
         bool v0 = m >= sp.lo && m < sp.hi;
         bool v1 = mb >= sp.lo && mb < sp.hi;
-        if (ODD) { // nodes next to an x face belong to the face kernel
+        bool lo0 = false, hi0 = false, lo1 = false, hi1 = false; // x-face nodes (XF)
+        uint32_t r0 = 0, r1 = 0;                                  // their rows
+        if (ODD) {
             const uint32_t nx = (uint32_t)G.nx;
-            const uint32_t xa = m - nx * fast_div(m, G.mag_nx), xb = mb - nx * fast_div(mb, G.mag_nx);
-            v0 = v0 && xa != 0u && xa != nx - 1u;
-            v1 = v1 && xb != 0u && xb != nx - 1u;
+            r0 = fast_div(m, G.mag_nx);
+            r1 = fast_div(mb, G.mag_nx);
+            const uint32_t xa = m - nx * r0, xb = mb - nx * r1;
+            if (XF) {
+                lo0 = v0 && xa == 0u;
+                hi0 = v0 && xa == nx - 1u;
+                lo1 = v1 && xb == 0u;
+                hi1 = v1 && xb == nx - 1u;
+            } else { // nodes next to an x face belong to the face kernel
+                v0 = v0 && xa != 0u && xa != nx - 1u;
+                v1 = v1 && xb != 0u && xb != nx - 1u;
+            }
         }
 
         const bool ok = mbar_wait(&bar[st], parity, T.budget);
@@ -270,21 +363,29 @@ __global__ void __launch_bounds__(kThreads, 2)
             if (!ODD) {
 #pragma unroll
                 for (int q = 0; q < 19; ++q)
-                    fl[q] = Pair<SF<S>>::ld(reinterpret_cast<const SF<S> *>(sb + Stage<S>::offset(q)) + o + sh[q]);
+                    fl[q] = PF<S>::ld(reinterpret_cast<const SF<S> *>(sb + Stage<S>::offset(q)) + o + sh[q]);
 #pragma unroll
                 for (int q = 0; q < 7; ++q)
-                    gl[q] = Pair<SG<S>>::ld(reinterpret_cast<const SG<S> *>(sb + Stage<S>::offset(19 + q)) + o +
+                    gl[q] = PG<S>::ld(reinterpret_cast<const SG<S> *>(sb + Stage<S>::offset(19 + q)) + o +
                                             sh[19 + q]);
             } else {
 #pragma unroll
                 for (int q = 0; q < 19; ++q) {
                     const SF<S> *w = reinterpret_cast<const SF<S> *>(sb + Stage<S>::offset(q)) + o + sh[q];
-                    fl[q] = make_float2(tof(w[0]), tof(w[32]));
+                    fl[q] = make_float2(PF<S>::one(w[0]), PF<S>::one(w[32]));
                 }
 #pragma unroll
                 for (int q = 0; q < 7; ++q) {
                     const SG<S> *w = reinterpret_cast<const SG<S> *>(sb + Stage<S>::offset(19 + q)) + o + sh[19 + q];
-                    gl[q] = make_float2(tof(w[0]), tof(w[32]));
+                    gl[q] = make_float2(PG<S>::one(w[0]), PG<S>::one(w[32]));
+                }
+                if (XF && (lo0 || hi0 || lo1 || hi1)) {
+                    const uint32_t *side = reinterpret_cast<const uint32_t *>(sb + Stage<S>::win);
+                    const uint32_t row0 = fast_div(sp.n0, G.mag_nx);
+                    if (lo0) xface_in<S, 0, 0>(fl, gl, side + 12u * (r0 - row0), m, G, P);
+                    if (hi0) xface_in<S, 1, 0>(fl, gl, side + 12u * (r0 - row0) + 6u, m, G, P);
+                    if (lo1) xface_in<S, 0, 1>(fl, gl, side + 12u * (r1 - row0), mb, G, P);
+                    if (hi1) xface_in<S, 1, 1>(fl, gl, side + 12u * (r1 - row0) + 6u, mb, G, P);
                 }
             }
             collide(P, fl, gl);
@@ -296,25 +397,37 @@ __global__ void __launch_bounds__(kThreads, 2)
                 // writes the first padding element, which no node reads
                 if (v0) {
 #pragma unroll
-                    for (int q = 0; q < 19; ++q) Pair<SF<S>>::st(fo + opp19(q) * s + m, fl[q]);
+                    for (int q = 0; q < 19; ++q) PF<S>::st(fo + opp19(q) * s + m, fl[q]);
                     const uint32_t rb0 = SRG(S) ? rnd_node(m, P.t) : 0u, rb1 = SRG(S) ? rnd_node(mb, P.t) : 0u;
 #pragma unroll
                     for (int q = 0; q < 7; ++q)
-                        Pair<SG<S>>::sts(go + opp7(q) * s + m, gl[q], rnd_pop(rb0, q), rnd_pop(rb1, q));
+                        PG<S>::sts(go + opp7(q) * s + m, gl[q], rnd_pop(rb0, q), rnd_pop(rb1, q));
                 }
             } else {
+                // a link that leaves an x-face node through its face is stored below instead
+                const bool p0 = v0 && !hi0, m0 = v0 && !lo0, p1 = v1 && !hi1, m1 = v1 && !lo1;
 #pragma unroll
                 for (int q = 0; q < 19; ++q) {
                     SF<S> *p = fo + q * s + (int64_t)m + G.off[q];
-                    if (v0) Pair<SF<S>>::st1(p, fl[q].x);
-                    if (v1) Pair<SF<S>>::st1(p + 32, fl[q].y);
+                    const bool c0 = ex19(q) > 0 ? p0 : ex19(q) < 0 ? m0 : v0;
+                    const bool c1 = ex19(q) > 0 ? p1 : ex19(q) < 0 ? m1 : v1;
+                    if (c0) PF<S>::st1(p, fl[q].x);
+                    if (c1) PF<S>::st1(p + 32, fl[q].y);
                 }
                 const uint32_t rb0 = SRG(S) ? rnd_node(m, P.t) : 0u, rb1 = SRG(S) ? rnd_node(mb, P.t) : 0u;
 #pragma unroll
                 for (int q = 0; q < 7; ++q) {
                     SG<S> *p = go + q * s + (int64_t)m + G.off[q];
-                    if (v0) Pair<SG<S>>::st1s(p, gl[q].x, rnd_pop(rb0, q));
-                    if (v1) Pair<SG<S>>::st1s(p + 32, gl[q].y, rnd_pop(rb1, q));
+                    const bool c0 = ex7(q) > 0 ? p0 : ex7(q) < 0 ? m0 : v0;
+                    const bool c1 = ex7(q) > 0 ? p1 : ex7(q) < 0 ? m1 : v1;
+                    if (c0) PG<S>::st1s(p, gl[q].x, rnd_pop(rb0, q));
+                    if (c1) PG<S>::st1s(p + 32, gl[q].y, rnd_pop(rb1, q));
+                }
+                if (XF && (lo0 || hi0 || lo1 || hi1)) {
+                    if (lo0) xface_out<S, 0, 0>(fo, go, fl, gl, m, rb0, G, P);
+                    if (hi0) xface_out<S, 1, 0>(fo, go, fl, gl, m, rb0, G, P);
+                    if (lo1) xface_out<S, 0, 1>(fo, go, fl, gl, mb, rb1, G, P);
+                    if (hi1) xface_out<S, 1, 1>(fo, go, fl, gl, mb, rb1, G, P);
                 }
             }
         }
@@ -334,19 +447,27 @@ __global__ void __launch_bounds__(kThreads, 2)
         if (warp == 0) {
             const uint32_t tn = t + (uint32_t)NST * gridDim.x;
             if (tn < ntiles)
-                issue_tile<S, ODD>(f, g, G, tile_span<ODD>(G, T, tn).n0, stages + st * Stage<S>::bytes,
-                                   shift + 26 * st, &bar[st], lane);
+                issue_tile<S, ODD, XF>(f, g, G, tile_span<ODD>(G, T, tn), stages + st * Stage<S>::bytes,
+                                       shift + 26 * st, &bar[st], lane);
         }
     }
 }
 
-template <int S> const void *staged_fn() { return reinterpret_cast<const void *>(&k_aa_staged<S, true>); }
-
-template <int S> cudaError_t staged_attr() {
+template <int S> cudaError_t staged_attr(int *blocks_per_sm) {
     const int b = Stage<S>::smem;
-    cudaError_t e = cudaFuncSetAttribute(k_aa_staged<S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_aa_staged<S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
-    return e;
+    const void *fn[3] = {reinterpret_cast<const void *>(&k_aa_staged<S, false, false>),
+                         reinterpret_cast<const void *>(&k_aa_staged<S, true, false>),
+                         reinterpret_cast<const void *>(&k_aa_staged<S, true, true>)};
+    int least = 1 << 30;
+    for (const void *k : fn) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+        int per = 0;
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, kThreads, b);
+        if (e != cudaSuccess) return e;
+        least = per < least ? per : least;
+    }
+    *blocks_per_sm = least;
+    return cudaSuccess;
 }
 
 template <int S> cudaError_t staged_launch(const StepArgs &a) {
@@ -354,13 +475,18 @@ template <int S> cudaError_t staged_launch(const StepArgs &a) {
     auto g = static_cast<SG<S> *>(a.g);
     const StagedGeom &T = a.T;
     if (a.parity == 0) {
-        k_aa_staged<S, false><<<T.grid, kThreads, Stage<S>::smem, a.stream>>>(f, g, a.G, a.P, T, a.err);
+        k_aa_staged<S, false, false><<<T.grid, kThreads, Stage<S>::smem, a.stream>>>(f, g, a.G, a.P, T, a.err);
         return cudaGetLastError();
     }
-    if (T.odd_tiles) k_aa_staged<S, true><<<T.grid, kThreads, Stage<S>::smem, a.stream>>>(f, g, a.G, a.P, T, a.err);
+    if (T.odd_tiles) {
+        if (T.xf) k_aa_staged<S, true, true><<<T.grid, kThreads, Stage<S>::smem, a.stream>>>(f, g, a.G, a.P, T, a.err);
+        else k_aa_staged<S, true, false><<<T.grid, kThreads, Stage<S>::smem, a.stream>>>(f, g, a.G, a.P, T, a.err);
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    return launch_face(a, a.nface); // every node next to a face
+    // the nodes next to a y or z face (and, for rows shorter than kXfMinNx,
+    // those next to an x face) go through the general face kernel
+    return launch_face(a, T.xf ? a.nface_yz : a.nface);
 }
 
 } // namespace
@@ -376,17 +502,15 @@ int staged_smem_bytes(int storage) {
 
 int staged_tile_nodes() { return kTile; }
 
+int staged_xf_min_nx() { return kXfMinNx; }
+
 cudaError_t staged_prepare(int storage, int *blocks_per_sm) {
-    cudaError_t e;
-    const void *fn;
     switch (storage) {
-    case ST_F32: e = staged_attr<ST_F32>(); fn = staged_fn<ST_F32>(); break;
-    case ST_F16: e = staged_attr<ST_F16>(); fn = staged_fn<ST_F16>(); break;
-    case ST_F16M: e = staged_attr<ST_F16M>(); fn = staged_fn<ST_F16M>(); break;
-    default: e = staged_attr<ST_BF16>(); fn = staged_fn<ST_BF16>(); break;
+    case ST_F32: return staged_attr<ST_F32>(blocks_per_sm);
+    case ST_F16: return staged_attr<ST_F16>(blocks_per_sm);
+    case ST_F16M: return staged_attr<ST_F16M>(blocks_per_sm);
+    default: return staged_attr<ST_BF16>(blocks_per_sm);
     }
-    if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, kThreads, staged_smem_bytes(storage));
 }
 
 cudaError_t launch_staged(const StepArgs &a) {

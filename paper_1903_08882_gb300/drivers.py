@@ -7,9 +7,60 @@ in the CUDA library.
 """
 from __future__ import annotations
 
+import json
 import math
+import os
+import time
 
 import numpy as np
+
+
+class RunLog:
+    """Append-only JSON-lines log of a run: one object per line with the
+    record kind, the wall-clock time and the given fields (numbers, strings,
+    lists; numpy values are converted).  Opened in append mode, so a resumed
+    run continues the same file.  Use as a context manager or call close()."""
+
+    def __init__(self, path: str):
+        self.path = path
+        d = os.path.dirname(os.path.abspath(path))
+        os.makedirs(d, exist_ok=True)
+        self._fh = open(path, "a")
+
+    @staticmethod
+    def _plain(v):
+        if isinstance(v, dict):
+            return {k: RunLog._plain(x) for k, x in v.items()}
+        if isinstance(v, (list, tuple)):
+            return [RunLog._plain(x) for x in v]
+        if isinstance(v, np.ndarray):
+            return v.tolist()
+        if isinstance(v, np.generic):
+            return v.item()
+        return v
+
+    def write(self, kind: str, **fields):
+        rec = {"kind": kind, "time": time.time()}
+        rec.update({k: self._plain(v) for k, v in fields.items()})
+        self._fh.write(json.dumps(rec) + "\n")
+        self._fh.flush()
+
+    def close(self):
+        if self._fh:
+            self._fh.close()
+            self._fh = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def read_log(path: str):
+    """The records of a RunLog file, in order."""
+    with open(path) as fh:
+        return [json.loads(line) for line in fh if line.strip()]
 
 
 def free_fall_steps(H: float, U: float) -> float:
@@ -18,7 +69,7 @@ def free_fall_steps(H: float, U: float) -> float:
 
 
 def run_to_steady(lat, every: int = 1000, tol: float = 1e-7, max_steps: int = 2_000_000, face: int = 0,
-                  min_steps: int = 0, average: int = 1):
+                  min_steps: int = 0, average: int = 1, log: RunLog | None = None):
     """Advance until the relative change of the Nusselt number of Dirichlet
     face `face` over `every` steps is below `tol` (the steady criterion on the
     hot-wall Nusselt number; Sec. 3 uses a field criterion instead).
@@ -28,7 +79,9 @@ def run_to_steady(lat, every: int = 1000, tol: float = 1e-7, max_steps: int = 2_
     last k samples.
     Returns dict(steps, converged, Nu, history, diag, diag_mean): diag is the
     last sample's diagnostics, diag_mean the wall Nusselt numbers (Nu_face,
-    Nu_link) averaged over the last k samples."""
+    Nu_link) averaged over the last k samples.  With a RunLog every sample is
+    written as a "sample" record (step, Nu, Re_rms, E) and the outcome as a
+    "steady" record."""
     k = max(1, int(average))
     lat.sample()
     prev = lat.diagnostics()["Nu_face"][face]
@@ -37,8 +90,12 @@ def run_to_steady(lat, every: int = 1000, tol: float = 1e-7, max_steps: int = 2_
     def done(converged, d):
         nu_face = np.mean([w[0] for w in walls[-k:]], axis=0)
         nu_link = np.mean([w[1] for w in walls[-k:]], axis=0)
-        return dict(steps=steps, converged=converged, Nu=float(np.mean(hist[-k:])), history=np.array(hist),
-                    diag=d, diag_mean=dict(Nu_face=nu_face, Nu_link=nu_link))
+        out = dict(steps=steps, converged=converged, Nu=float(np.mean(hist[-k:])), history=np.array(hist),
+                   diag=d, diag_mean=dict(Nu_face=nu_face, Nu_link=nu_link))
+        if log is not None:
+            log.write("steady", steps=steps, converged=converged, Nu=out["Nu"], tol=tol, average=k,
+                      Nu_face=nu_face, Nu_link=nu_link)
+        return out
 
     while steps < max_steps:
         lat.step(every)
@@ -47,6 +104,8 @@ def run_to_steady(lat, every: int = 1000, tol: float = 1e-7, max_steps: int = 2_
         d = lat.diagnostics(reset=True)
         hist.append(d["Nu_face"][face])
         walls.append((np.array(d["Nu_face"]), np.array(d.get("Nu_link", d["Nu_face"]))))
+        if log is not None:
+            log.write("sample", step=steps, Nu=d["Nu_face"][face], Re_rms=d.get("Re_rms"), E=d.get("E"))
         walls = walls[-k:]
         if len(hist) > 2 * k and steps >= min_steps:
             new, old = float(np.mean(hist[-k:])), float(np.mean(hist[-2 * k:-k]))

@@ -75,7 +75,8 @@ class LbmDiag(ctypes.Structure):
 
 
 class LbmSchedule(ctypes.Structure):
-    _fields_ = [("block_size", c_int), ("blocks_per_sm", c_int), ("steps_per_launch", c_int), ("graph_chunk", c_int)]
+    _fields_ = [("block_size", c_int), ("blocks_per_sm", c_int), ("steps_per_launch", c_int), ("graph_chunk", c_int),
+                ("tile_span", c_int), ("mode", c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -429,8 +430,9 @@ def lbm_batch_get_schedule(batch) -> dict:
     return s.as_dict()
 
 
-def lbm_batch_set_schedule(batch, block_size=256, blocks_per_sm=2, steps_per_launch=100, graph_chunk=1000):
-    s = LbmSchedule(block_size, blocks_per_sm, steps_per_launch, graph_chunk)
+def lbm_batch_set_schedule(batch, block_size=256, blocks_per_sm=2, steps_per_launch=100, graph_chunk=1000,
+                           tile_span=1, mode=0):
+    s = LbmSchedule(block_size, blocks_per_sm, steps_per_launch, graph_chunk, tile_span, mode)
     _bcheck(lib().lbm_batch_set_schedule(batch, ctypes.byref(s)))
 
 

@@ -350,3 +350,22 @@ def test_run_to_steady_averaged_criterion_with_noise():
     assert r["converged"]
     assert abs(r["Nu"] - 8.8) / 8.8 < 1e-4
     assert 0.5 * np.exp(-r["steps"] / 2e4) < 1e-4 * 8.8
+
+
+def test_run_log_records_a_steady_run(tmp_path):
+    """drivers.RunLog: JSON lines, one per sample and one for the outcome of
+    run_to_steady; appending to an existing file keeps the earlier records."""
+    from paper_1903_08882_gb300 import drivers
+
+    path = str(tmp_path / "runs" / "steady.jsonl")
+    with drivers.RunLog(path) as log:
+        log.write("config", N=65, Ra=1e6, Pr=0.71, storage="fp32", walls=[(1, 0.5), (1, -0.5)])
+        r = drivers.run_to_steady(_RelaxingNu(), every=1000, tol=1e-7, max_steps=10**6, log=log)
+    recs = drivers.read_log(path)
+    assert recs[0]["kind"] == "config" and recs[0]["walls"] == [[1, 0.5], [1, -0.5]]
+    samples = [x for x in recs if x["kind"] == "sample"]
+    assert len(samples) == r["steps"] // 1000 and samples[-1]["step"] == r["steps"]
+    assert recs[-1]["kind"] == "steady" and recs[-1]["converged"] and recs[-1]["Nu"] == r["Nu"]
+    with drivers.RunLog(path) as log:
+        log.write("note", text="resumed")
+    assert len(drivers.read_log(path)) == len(recs) + 1

@@ -46,8 +46,9 @@ def _make(lbm, storage="fp32"):
     return lats
 
 
+@pytest.mark.parametrize("span", [1, 3])
 @pytest.mark.parametrize("storage", ["fp32", "fp16s", "fp16m"])
-def test_batch_matches_single_cells(lbm, storage):
+def test_batch_matches_single_cells(lbm, storage, span):
     import torch
 
     stream = torch.cuda.Stream()
@@ -57,7 +58,7 @@ def test_batch_matches_single_cells(lbm, storage):
         for lat in ref:
             lat.step(37)
         with lbm.Batch(bat, stream=stream) as b:
-            b.set_schedule(block_size=128, blocks_per_sm=2, steps_per_launch=5, graph_chunk=10)
+            b.set_schedule(block_size=128, blocks_per_sm=2, steps_per_launch=5, graph_chunk=10, tile_span=span)
             b.step(37)  # three graph replays and seven steps launched directly
         for r, x in zip(ref, bat):
             fr, gr = r.populations()
