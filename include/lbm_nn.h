@@ -11,7 +11,10 @@
  * Conventions: activations are FP32, one sample, channel-major [C][D][H][W]
  * with W fastest; convolution weights are BF16 [Cout][Cin][27] (taps ordered
  * dz, dy, dx each in -1, 0, 1, dx fastest) with FP32 accumulation and an FP32
- * bias.  All pointers are device pointers; every call is asynchronous on
+ * bias.  The convolutions run on the tensor cores (BF16 x BF16 -> FP32): an
+ * FP32 activation or gradient operand enters as the sum of two BF16 terms
+ * (relative error at most 2^-18 per operand), so results agree with an FP32
+ * convolution of the same BF16 weights to about 1e-6 relative.  All pointers are device pointers; every call is asynchronous on
  * `stream` (NULL: legacy default stream) and returns an lbm_status
  * (lbm_last_error(NULL) describes a failure).  Sizes must be positive.
  */
@@ -39,7 +42,9 @@ lbm_status lbm_nn_conv3d_backward_data(const float *dy, int Cout, int D, int H, 
                                        uint16_t *w_t_bf16, int Cin, float *dx, int accumulate, void *stream);
 
 /* dw[co][ci][tap] += sum_voxels dy[co][voxel] x[ci][voxel + tap];
- * db[co] += sum_voxels dy[co][voxel]  (FP32, accumulated). */
+ * db[co] += sum_voxels dy[co][voxel]  (FP32, accumulated by atomic adds, so
+ * the low bits depend on the order blocks finish; db may be NULL).
+ * Cin <= 128 (LBM_ERR_PARAM otherwise). */
 lbm_status lbm_nn_conv3d_backward_weight(const float *x, int Cin, int D, int H, int W, const float *dy, int Cout,
                                          float *dw, float *db, void *stream);
 

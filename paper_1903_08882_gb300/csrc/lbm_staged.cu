@@ -361,13 +361,14 @@ __global__ void __launch_bounds__(kThreads, 2)
             const int *sh = shift + 26 * st;
             float2 fl[19], gl[7];
             if (!ODD) {
+                // even tiles start on a 1024-byte boundary of every array, so the
+                // windows are not shifted (shift[q] = 0)
 #pragma unroll
                 for (int q = 0; q < 19; ++q)
-                    fl[q] = PF<S>::ld(reinterpret_cast<const SF<S> *>(sb + Stage<S>::offset(q)) + o + sh[q]);
+                    fl[q] = PF<S>::ld(reinterpret_cast<const SF<S> *>(sb + Stage<S>::offset(q)) + o);
 #pragma unroll
                 for (int q = 0; q < 7; ++q)
-                    gl[q] = PG<S>::ld(reinterpret_cast<const SG<S> *>(sb + Stage<S>::offset(19 + q)) + o +
-                                            sh[19 + q]);
+                    gl[q] = PG<S>::ld(reinterpret_cast<const SG<S> *>(sb + Stage<S>::offset(19 + q)) + o);
             } else {
 #pragma unroll
                 for (int q = 0; q < 19; ++q) {

@@ -1,14 +1,15 @@
 // Kernels of the warm-start network (declared in include/lbm_nn.h): 3x3x3
-// convolutions with BF16 weights and FP32 accumulation (forward, data
+// convolutions on the tensor cores with FP32 accumulation (forward, data
 // gradient, weight gradient), ReLU backward, ceil average pooling, nearest
 // upsampling, trilinear interpolation, MSE loss, Adam.
 //
-// Convolution forward: one thread per output voxel and eight output channels;
-// the block stages the weights of its eight output channels for sixteen input
-// channels at a time in shared memory as [ci][tap][co] (so a thread reads the
-// eight weights of one (ci, tap) as two 16-byte words); input voxels come
-// through L1, where the 27-point neighbourhoods of a block's 256 consecutive
-// voxels overlap.
+// The convolutions are implicit GEMMs on mma.sync (m16n8k16, BF16 x BF16 ->
+// FP32): forward and data gradient (a forward convolution of the output
+// gradient with the flipped, transposed weights) take voxels as GEMM rows and
+// output channels as columns; the weight gradient takes output channels by
+// input channels per tap, reducing over voxels.  The weights are BF16; an
+// FP32 activation or gradient operand enters as the sum of two BF16 terms
+// (see split_bf16), so the products carry FP32-level accuracy.
 #include <cuda_bf16.h>
 
 #include <string>
@@ -19,12 +20,7 @@
 namespace {
 
 constexpr int kT = 256; // threads per block
-constexpr int kCO = 8;  // output channels per thread
-constexpr int kCI = 16; // input channels staged per round
 
-__device__ __forceinline__ float bf(const uint16_t u) {
-    return __uint_as_float(static_cast<uint32_t>(u) << 16);
-}
 
 struct Vox {
     int z, y, x;
@@ -51,62 +47,241 @@ __device__ __forceinline__ uint32_t tap_mask(const Vox &p, int D, int H, int W) 
     return m;
 }
 
-__global__ void __launch_bounds__(kT) k_conv_fwd(const float *__restrict__ x, int Cin, int D, int H, int W,
-                                                 const uint16_t *__restrict__ w, const float *__restrict__ bias,
-                                                 int Cout, float *__restrict__ y, int relu, int accumulate) {
-    __shared__ __align__(16) float ws[kCI][27][kCO];
-    const int64_t V = (int64_t)D * H * W;
-    const int64_t v = (int64_t)blockIdx.x * kT + threadIdx.x;
-    const int co0 = blockIdx.y * kCO;
-    const bool live = v < V;
-    Vox p{0, 0, 0};
-    uint32_t mask = 0;
-    if (live) {
-        p = vox(v, H, W);
-        mask = tap_mask(p, D, H, W);
-    }
-    const int64_t HW = (int64_t)H * W;
-    float acc[kCO];
+// ------------------------------------------------ tensor-core convolutions ----
+//
+// Implicit GEMM on the tensor cores: mma.sync.m16n8k16 with BF16 operands and
+// FP32 accumulation.  An FP32 operand x is split into hi = bf16(x) and
+// lo = bf16(x - hi) (both nearest even; x - hi is exact in FP32) and enters
+// as two products, after the BF16 splitting of Henry, Tang and Heinecke
+// (ARITH 2019): |x - hi - lo| <= 2^-18 |x|.  Weights are BF16 already, so the
+// forward and data-gradient products take two MMAs; the weight gradient,
+// with both operands FP32, takes hi*hi + hi*lo + lo*hi (the dropped lo*lo is
+// below 2^-16 of the product).  Sums stay FP32.
+//
+// Fragment layout of m16n8k16 (g = lane / 4, q = lane % 4; each 32-bit
+// register holds two BF16, the lower index in the low half):
+//   A (16 x 16, row-major): {a0,a1} = (g, 2q..2q+1), {a2,a3} = (g+8, 2q..2q+1),
+//                           {a4,a5} = (g, 2q+8..2q+9), {a6,a7} = (g+8, 2q+8..2q+9)
+//   B (16 x 8, k by n):     {b0,b1} = (2q..2q+1, g), {b2,b3} = (2q+8..2q+9, g)
+//   C (16 x 8, FP32):       c0, c1 = (g, 2q..2q+1), c2, c3 = (g+8, 2q..2q+1)
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+    uint32_t r;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+// Two FP32 values as BF16 pairs hi (nearest) and lo (nearest of the rest).
+struct Split2 {
+    uint32_t hi, lo;
+};
+__device__ __forceinline__ Split2 split_bf16(float a, float b) {
+    Split2 r;
+    r.hi = pack_bf16(a, b);
+    const float ah = __uint_as_float(r.hi << 16), bh = __uint_as_float(r.hi & 0xFFFF0000u);
+    r.lo = pack_bf16(a - ah, b - bh);
+    return r;
+}
+__device__ __forceinline__ uint32_t pack_u16(uint16_t lo, uint16_t hi) {
+    return (uint32_t)lo | ((uint32_t)hi << 16);
+}
+__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, "
+                 "{%8, %9}, {%0, %1, %2, %3};"
+                 : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+constexpr int kTcWarps = 8;            // warps per block
+constexpr int kTcM = 16 * kTcWarps;    // output voxels per block (16 per warp)
+constexpr int kTcN = 32;               // output channels per block (4 n-tiles of 8)
+constexpr int kTcChunk = 16;           // input channels staged at a time (one k-step)
+constexpr int kTcPitch = kTcN + 8;     // words per staged weight row: the fragment reads hit 32 banks
+
+// y[co][v] = bias + sum_{ci, tap} w[co][ci][tap] x[ci][v + tap]: rows of the
+// GEMM are voxels, columns output channels, the reduction runs over taps and
+// 16-channel chunks.  The block stages the weights of its kTcN output
+// channels for all 27 taps of one chunk in shared memory, as channel pairs
+// ([tap][ci / 2][co] words, the lower channel in the low half), so a B
+// fragment register is one 32-bit read; each warp builds its A fragments
+// straight from global memory (the taps of neighbouring voxels overlap in
+// L1) and reuses them for its four n-tiles.
+__global__ void __launch_bounds__(32 * kTcWarps) k_conv_fwd_tc(const float *__restrict__ x, int Cin, int D, int H,
+                                                               int W, const uint16_t *__restrict__ w,
+                                                               const float *__restrict__ bias, int Cout,
+                                                               float *__restrict__ y, int relu, int accumulate) {
+    __shared__ uint32_t wt[27][kTcChunk / 2][kTcPitch];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, q = lane & 3;
+    const int64_t V = (int64_t)D * H * W, HW = (int64_t)H * W;
+    const int co0 = blockIdx.y * kTcN;
+    const int64_t v0 = (int64_t)blockIdx.x * kTcM + warp * 16;
+    // the warp's two voxel rows g and g + 8: positions and in-range taps
+    const int64_t va = v0 + g, vb = v0 + g + 8;
+    const bool la = va < V, lb = vb < V;
+    const uint32_t ma = la ? tap_mask(vox(va, H, W), D, H, W) : 0u;
+    const uint32_t mb = lb ? tap_mask(vox(vb, H, W), D, H, W) : 0u;
+    float acc[4][4];
 #pragma unroll
-    for (int c = 0; c < kCO; ++c) acc[c] = (bias && co0 + c < Cout) ? bias[co0 + c] : 0.f;
-    for (int ci0 = 0; ci0 < Cin; ci0 += kCI) {
-        __syncthreads();
-        for (int k = threadIdx.x; k < kCI * 27 * kCO; k += kT) {
-            const int c = k % kCO, t = (k / kCO) % 27, ci = k / (kCO * 27);
-            const bool ok = co0 + c < Cout && ci0 + ci < Cin;
-            ws[ci][t][c] = ok ? bf(w[((int64_t)(co0 + c) * Cin + ci0 + ci) * 27 + t]) : 0.f;
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) acc[j][i] = 0.f;
+    for (int ci_base = 0; ci_base < Cin; ci_base += kTcChunk) {
+        const int cspan = Cin - ci_base < kTcChunk ? Cin - ci_base : kTcChunk;
+        __syncthreads(); // the previous chunk's weights are no longer read
+        for (int k = threadIdx.x; k < 27 * (kTcChunk / 2) * kTcN; k += blockDim.x) {
+            const int c = k % kTcN, r = k / kTcN, pr = r % (kTcChunk / 2), t = r / (kTcChunk / 2);
+            const int ci = 2 * pr, co = co0 + c;
+            uint16_t lo = 0, hi = 0;
+            if (co < Cout) {
+                const uint16_t *wc = w + ((int64_t)co * Cin + ci_base + ci) * 27 + t;
+                if (ci < cspan) lo = wc[0];
+                if (ci + 1 < cspan) hi = wc[27];
+            }
+            wt[t][pr][c] = pack_u16(lo, hi);
         }
         __syncthreads();
-        if (!live) continue;
-        const int cmax = Cin - ci0 < kCI ? Cin - ci0 : kCI;
-        for (int ci = 0; ci < cmax; ++ci) {
-            const float *xc = x + (int64_t)(ci0 + ci) * V + v;
+        // the channels this lane's A fragment holds: 2q, 2q+1, 2q+8, 2q+9
+        const float *xc[4];
+        bool cok[4];
 #pragma unroll
-            for (int t = 0; t < 27; ++t) {
-                const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
-                const float xv = ((mask >> t) & 1u) ? xc[dz * HW + dy * W + dx] : 0.f;
-                const float4 wa = *reinterpret_cast<const float4 *>(&ws[ci][t][0]);
-                const float4 wb = *reinterpret_cast<const float4 *>(&ws[ci][t][4]);
-                acc[0] = fmaf(wa.x, xv, acc[0]);
-                acc[1] = fmaf(wa.y, xv, acc[1]);
-                acc[2] = fmaf(wa.z, xv, acc[2]);
-                acc[3] = fmaf(wa.w, xv, acc[3]);
-                acc[4] = fmaf(wb.x, xv, acc[4]);
-                acc[5] = fmaf(wb.y, xv, acc[5]);
-                acc[6] = fmaf(wb.z, xv, acc[6]);
-                acc[7] = fmaf(wb.w, xv, acc[7]);
+        for (int u = 0; u < 4; ++u) {
+            const int c = 2 * q + (u & 1) + (u >> 1) * 8;
+            cok[u] = c < cspan;
+            xc[u] = x + (int64_t)(ci_base + (cok[u] ? c : 0)) * V;
+        }
+#pragma unroll 3
+        for (int t = 0; t < 27; ++t) {
+            const int dz = t / 9 - 1, dyy = (t / 3) % 3 - 1, dx = t % 3 - 1;
+            const int64_t off = dz * HW + dyy * W + dx;
+            const bool ta = (ma >> t) & 1u, tb = (mb >> t) & 1u;
+            float xa[4], xb[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                xa[u] = (cok[u] && ta) ? xc[u][va + off] : 0.f;
+                xb[u] = (cok[u] && tb) ? xc[u][vb + off] : 0.f;
+            }
+            const Split2 s0 = split_bf16(xa[0], xa[1]), s1 = split_bf16(xb[0], xb[1]),
+                         s2 = split_bf16(xa[2], xa[3]), s3 = split_bf16(xb[2], xb[3]);
+            const uint32_t ah[4] = {s0.hi, s1.hi, s2.hi, s3.hi}, al[4] = {s0.lo, s1.lo, s2.lo, s3.lo};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const uint32_t b0 = wt[t][q][j * 8 + g], b1 = wt[t][q + 4][j * 8 + g];
+                mma_bf16(acc[j], al, b0, b1);
+                mma_bf16(acc[j], ah, b0, b1);
             }
         }
     }
-    if (!live) return;
 #pragma unroll
-    for (int c = 0; c < kCO; ++c) {
-        if (co0 + c >= Cout) break;
-        float r = acc[c];
-        float *out = y + (int64_t)(co0 + c) * V + v;
-        if (accumulate) r += *out;
-        if (relu) r = fmaxf(r, 0.f);
-        *out = r;
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int co = co0 + j * 8 + 2 * q + (i & 1);
+            const int64_t v = (i < 2) ? va : vb;
+            if (co >= Cout || v >= V) continue;
+            float r = acc[j][i] + (bias ? bias[co] : 0.f);
+            float *out = y + (int64_t)co * V + v;
+            if (accumulate) r += *out;
+            if (relu) r = fmaxf(r, 0.f);
+            *out = r;
+        }
+}
+
+// dw[co][ci][tap] += sum_v dy[co][v] x[ci][v + tap]: for each tap a GEMM of
+// output channels (rows, one 16-channel m-tile per block) by input channels
+// (columns, all of them: up to kTcNtMax n-tiles of 8) over voxels.  Block
+// (row batch, tap, m-tile): its warps take the rows (z, y) of the batch in
+// turn and walk each along x in steps of 16 voxels, so the tap's range
+// check is per row plus the x edges; the A fragment (dy) of a step serves
+// every n-tile.  The warps' sums meet in shared memory, then go to dw with
+// one atomic add per element.  NT >= ceil(Cin / 8) sizes the accumulators.
+constexpr int kTcNtMax = 16; // n-tiles per warp: 16 x 8 = 128 input channels
+template <int NT>
+__global__ void __launch_bounds__(32 * kTcWarps) k_conv_bww_tc(const float *__restrict__ x, int Cin, int D, int H,
+                                                               int W, const float *__restrict__ dy, int Cout,
+                                                               float *__restrict__ dw, int rows_per_block) {
+    __shared__ float red[16][8 * NT];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane >> 2, q = lane & 3;
+    const int t = blockIdx.y, co0 = blockIdx.z * 16;
+    const int dz = t / 9 - 1, dyy = (t / 3) % 3 - 1, dx = t % 3 - 1;
+    const int64_t V = (int64_t)D * H * W, HW = (int64_t)H * W;
+    const int nrows = D * H, nt = (Cin + 7) / 8;
+    for (int k = threadIdx.x; k < 16 * 8 * NT; k += blockDim.x) (&red[0][0])[k] = 0.f;
+    float acc[NT][4];
+#pragma unroll
+    for (int j = 0; j < NT; ++j)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) acc[j][i] = 0.f;
+    const int r0 = blockIdx.x * rows_per_block, r1 = min(nrows, r0 + rows_per_block);
+    const bool coa = co0 + g < Cout, cob = co0 + g + 8 < Cout;
+    const float *dya = dy + (int64_t)(coa ? co0 + g : 0) * V, *dyb = dy + (int64_t)(cob ? co0 + g + 8 : 0) * V;
+    for (int r = r0 + warp; r < r1; r += kTcWarps) {
+        const int z = r / H, yy = r - z * H;
+        const bool row_ok = z + dz >= 0 && z + dz < D && yy + dyy >= 0 && yy + dyy < H;
+        const int64_t rb = (int64_t)z * HW + (int64_t)yy * W; // row start
+        const int64_t sb = rb + dz * HW + dyy * W + dx;       // shifted row start
+        for (int x0 = 0; x0 < W; x0 += 16) {
+            // A fragment: dy[co][row, x0 + k] for k = 2q, 2q+1, 2q+8, 2q+9
+            float fa[4], fb[4];
+            bool kin[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int xk = x0 + 2 * q + (u & 1) + (u >> 1) * 8;
+                const bool in = xk < W;
+                fa[u] = (in && coa) ? dya[rb + xk] : 0.f;
+                fb[u] = (in && cob) ? dyb[rb + xk] : 0.f;
+                kin[u] = row_ok && in && xk + dx >= 0 && xk + dx < W;
+            }
+            const Split2 s0 = split_bf16(fa[0], fa[1]), s1 = split_bf16(fb[0], fb[1]),
+                         s2 = split_bf16(fa[2], fa[3]), s3 = split_bf16(fb[2], fb[3]);
+            const uint32_t ah[4] = {s0.hi, s1.hi, s2.hi, s3.hi}, al[4] = {s0.lo, s1.lo, s2.lo, s3.lo};
+            // B fragment of n-tile j: x[ci][row + tap, x0 + k] for ci = 8 j + g
+            const float *xs = x + sb + x0 + 2 * q;
+#pragma unroll
+            for (int j = 0; j < NT; ++j) {
+                if (j >= nt) break; // warp-uniform
+                const int ci = j * 8 + g;
+                const float *xc = xs + (int64_t)(ci < Cin ? ci : 0) * V;
+                float xv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) xv[u] = (ci < Cin && kin[u]) ? xc[(u & 1) + (u >> 1) * 8] : 0.f;
+                const Split2 b = split_bf16(xv[0], xv[1]), c = split_bf16(xv[2], xv[3]);
+                mma_bf16(acc[j], al, b.hi, c.hi);
+                mma_bf16(acc[j], ah, b.lo, c.lo);
+                mma_bf16(acc[j], ah, b.hi, c.hi);
+            }
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+        if (j >= nt) break;
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            if (acc[j][i] != 0.f) atomicAdd(&red[g + (i < 2 ? 0 : 8)][j * 8 + 2 * q + (i & 1)], acc[j][i]);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < 16 * Cin; k += blockDim.x) {
+        const int m = k / Cin, ci = k - m * Cin, co = co0 + m;
+        const float v = red[m][ci];
+        if (co < Cout && v != 0.f) atomicAdd(&dw[((int64_t)co * Cin + ci) * 27 + t], v);
+    }
+}
+
+// db[co] += sum_v dy[co][v] (FP32 gradients, not rounded).
+__global__ void __launch_bounds__(kT) k_bias_grad(const float *__restrict__ dy, int64_t V, float *__restrict__ db,
+                                                 int64_t chunk) {
+    __shared__ float red[kT / 32];
+    const int co = blockIdx.y;
+    const int64_t v0 = (int64_t)blockIdx.x * chunk, v1 = v0 + chunk < V ? v0 + chunk : V;
+    float s = 0.f;
+    for (int64_t v = v0 + threadIdx.x; v < v1; v += kT) s += dy[(int64_t)co * V + v];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float b = 0.f;
+        for (int k = 0; k < kT / 32; ++k) b += red[k];
+        atomicAdd(&db[co], b);
     }
 }
 
@@ -121,53 +296,6 @@ __global__ void k_flip_transpose(const uint16_t *__restrict__ w, uint16_t *__res
     wt[((int64_t)ci * Cout + co) * 27 + (26 - t)] = w[k];
 }
 
-__device__ __forceinline__ float warp_sum_f(float v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// One block per (voxel chunk, co, ci): 27 tap sums over the chunk, reduced in
-// the block and added to dw; the ci == 0 blocks also add the bias gradient.
-__global__ void __launch_bounds__(kT) k_conv_bww(const float *__restrict__ x, int Cin, int D, int H, int W,
-                                                 const float *__restrict__ dy, int Cout, float *__restrict__ dw,
-                                                 float *__restrict__ db, int64_t chunk) {
-    __shared__ float red[kT / 32][28];
-    const int co = blockIdx.y, ci = blockIdx.z;
-    const int64_t V = (int64_t)D * H * W, HW = (int64_t)H * W;
-    const int64_t v0 = (int64_t)blockIdx.x * chunk;
-    const int64_t v1 = v0 + chunk < V ? v0 + chunk : V;
-    float acc[28];
-#pragma unroll
-    for (int t = 0; t < 28; ++t) acc[t] = 0.f;
-    const float *xc = x + (int64_t)ci * V;
-    const float *gc = dy + (int64_t)co * V;
-    for (int64_t v = v0 + threadIdx.x; v < v1; v += kT) {
-        const float gv = gc[v];
-        const Vox p = vox(v, H, W);
-        const uint32_t mask = tap_mask(p, D, H, W);
-#pragma unroll
-        for (int t = 0; t < 27; ++t) {
-            const int dz = t / 9 - 1, dyy = (t / 3) % 3 - 1, dx = t % 3 - 1;
-            const float xv = ((mask >> t) & 1u) ? xc[v + dz * HW + dyy * W + dx] : 0.f;
-            acc[t] = fmaf(gv, xv, acc[t]);
-        }
-        acc[27] += gv;
-    }
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-    for (int t = 0; t < 28; ++t) {
-        const float s = warp_sum_f(acc[t]);
-        if (lane == 0) red[wid][t] = s;
-    }
-    __syncthreads();
-    if (threadIdx.x < 28) {
-        float s = 0.f;
-        for (int k = 0; k < kT / 32; ++k) s += red[k][threadIdx.x];
-        if (threadIdx.x < 27) atomicAdd(&dw[((int64_t)co * Cin + ci) * 27 + threadIdx.x], s);
-        else if (ci == 0 && db) atomicAdd(&db[co], s);
-    }
-}
 
 __global__ void k_relu_bwd(float *__restrict__ dy, const float *__restrict__ y, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -355,8 +483,8 @@ lbm_status lbm_nn_conv3d_forward(const float *x, int Cin, int D, int H, int W, c
                                  int Cout, float *y, int relu, void *stream) {
     if (!x || !w || !y || Cin < 1 || Cout < 1 || D < 1 || H < 1 || W < 1) return bad("lbm_nn_conv3d_forward");
     const int64_t V = (int64_t)D * H * W;
-    dim3 grid((unsigned)((V + kT - 1) / kT), (unsigned)((Cout + kCO - 1) / kCO));
-    k_conv_fwd<<<grid, kT, 0, S(stream)>>>(x, Cin, D, H, W, w, bias, Cout, y, relu, 0);
+    dim3 grid((unsigned)((V + kTcM - 1) / kTcM), (unsigned)((Cout + kTcN - 1) / kTcN));
+    k_conv_fwd_tc<<<grid, 32 * kTcWarps, 0, S(stream)>>>(x, Cin, D, H, W, w, bias, Cout, y, relu, 0);
     return done(cudaGetLastError(), "lbm_nn_conv3d_forward");
 }
 
@@ -367,20 +495,31 @@ lbm_status lbm_nn_conv3d_backward_data(const float *dy, int Cout, int D, int H, 
     const int64_t nw = (int64_t)Cout * Cin * 27;
     k_flip_transpose<<<(unsigned)((nw + kT - 1) / kT), kT, 0, S(stream)>>>(w, wt, Cout, Cin);
     const int64_t V = (int64_t)D * H * W;
-    dim3 grid((unsigned)((V + kT - 1) / kT), (unsigned)((Cin + kCO - 1) / kCO));
-    k_conv_fwd<<<grid, kT, 0, S(stream)>>>(dy, Cout, D, H, W, wt, nullptr, Cin, dx, 0, accumulate);
+    dim3 grid((unsigned)((V + kTcM - 1) / kTcM), (unsigned)((Cin + kTcN - 1) / kTcN));
+    k_conv_fwd_tc<<<grid, 32 * kTcWarps, 0, S(stream)>>>(dy, Cout, D, H, W, wt, nullptr, Cin, dx, 0, accumulate);
     return done(cudaGetLastError(), "lbm_nn_conv3d_backward_data");
 }
 
 lbm_status lbm_nn_conv3d_backward_weight(const float *x, int Cin, int D, int H, int W, const float *dy, int Cout,
                                          float *dw, float *db, void *stream) {
-    if (!x || !dy || !dw || Cin < 1 || Cout < 1 || D < 1 || H < 1 || W < 1 || Cin > 65535)
+    if (!x || !dy || !dw || Cin < 1 || Cout < 1 || D < 1 || H < 1 || W < 1 || Cin > 8 * kTcNtMax)
         return bad("lbm_nn_conv3d_backward_weight");
     const int64_t V = (int64_t)D * H * W;
-    const int64_t chunk = (int64_t)kT * 32;
-    dim3 grid((unsigned)((V + chunk - 1) / chunk), (unsigned)Cout, (unsigned)Cin);
-    k_conv_bww<<<grid, kT, 0, S(stream)>>>(x, Cin, D, H, W, dy, Cout, dw, db, chunk);
-    return done(cudaGetLastError(), "lbm_nn_conv3d_backward_weight");
+    const int nrows = D * H;
+    const int rpb = nrows / 64 > 32 ? nrows / 64 : 32; // about 64 row batches per tap and channel tile
+    dim3 grid((unsigned)((nrows + rpb - 1) / rpb), 27u, (unsigned)((Cout + 15) / 16));
+    const int nt = (Cin + 7) / 8;
+    auto kern = nt <= 1 ? k_conv_bww_tc<1> : nt <= 2 ? k_conv_bww_tc<2> : nt <= 4 ? k_conv_bww_tc<4>
+              : nt <= 8 ? k_conv_bww_tc<8> : k_conv_bww_tc<16>;
+    kern<<<grid, 32 * kTcWarps, 0, S(stream)>>>(x, Cin, D, H, W, dy, Cout, dw, rpb);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && db) {
+        const int64_t chunk = (int64_t)kT * 64;
+        dim3 gb((unsigned)((V + chunk - 1) / chunk), (unsigned)Cout);
+        k_bias_grad<<<gb, kT, 0, S(stream)>>>(dy, V, db, chunk);
+        e = cudaGetLastError();
+    }
+    return done(e, "lbm_nn_conv3d_backward_weight");
 }
 
 lbm_status lbm_nn_relu_backward(float *dy, const float *y, int64_t n, void *stream) {

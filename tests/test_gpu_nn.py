@@ -1,8 +1,11 @@
 """Warm-start network kernels on the GPU against the FP64 CPU reference
 (oracle/unet_ref.py): each layer operation forward and backward, Adam, and
-the whole network's output and parameter gradients.  Tolerance: FP32
-accumulation over at most ~3000 products per output (relative 1e-5 of the
-output scale); the weights are the same BF16 values on both sides."""
+the whole network's output and parameter gradients.  Tolerance: relative
+2e-5 of the output scale for one convolution, 1e-5 for the network's output:
+FP32 accumulation on the tensor cores (whose additions need not round to
+nearest) over up to 27 x 130 products whose magnitudes add to several times
+the output, each with its FP32 operand carried as two BF16 terms (relative
+error <= 2^-18); the weights are the same BF16 values on both sides."""
 import numpy as np
 import pytest
 
@@ -36,7 +39,11 @@ def _rel(a, b):
     return (a.double().cpu() - b).abs().max().item() / max(b.abs().max().item(), 1e-30)
 
 
-@pytest.mark.parametrize("cin,cout,size", [(3, 5, (7, 6, 5)), (19, 13, (9, 4, 11)), (48, 16, (17, 17, 17))])
+@pytest.mark.parametrize(
+    "cin,cout,size",
+    [(3, 5, (7, 6, 5)), (19, 13, (9, 4, 11)), (48, 16, (17, 17, 17)), (112, 48, (9, 9, 9)), (7, 37, (1, 3, 21)),
+     (130, 5, (3, 4, 5))],
+)
 def test_conv_forward_backward(U, cin, cout, size):
     g = torch.Generator().manual_seed(cin * 100 + cout)
     x = torch.rand((cin,) + size, generator=g, dtype=torch.float64) - 0.5
@@ -54,18 +61,22 @@ def test_conv_forward_backward(U, cin, cout, size):
     U.to_bf16(w.float().cuda(), wb)
     y = torch.empty((cout,) + size, device="cuda")
     U.conv_forward(xd, wb, b.float().cuda(), cout, y, relu=False)
-    assert _rel(y, yr.detach()) < 1e-5
+    assert _rel(y, yr.detach()) < 2e-5
     yrelu = torch.empty_like(y)
     U.conv_forward(xd, wb, b.float().cuda(), cout, yrelu, relu=True)
     assert torch.equal(yrelu, torch.clamp(y, min=0))
     dx = torch.empty_like(xd)
     scratch = torch.empty(cout * cin * 27, dtype=torch.int16, device="cuda")
     U.conv_backward_data(gyd, wb, scratch, cin, dx)
-    assert _rel(dx, xr.grad) < 1e-5
+    assert _rel(dx, xr.grad) < 2e-5
     dw = torch.zeros((cout, cin, 27), device="cuda")
     db = torch.zeros(cout, device="cuda")
+    if cin > 128:  # the weight gradient takes at most 128 input channels
+        with pytest.raises(RuntimeError):
+            U.conv_backward_weight(xd, gyd, dw, db)
+        return
     U.conv_backward_weight(xd, gyd, dw, db)
-    assert _rel(dw, wr.grad) < 1e-5 and _rel(db, br.grad) < 1e-5
+    assert _rel(dw, wr.grad) < 2e-5 and _rel(db, br.grad) < 2e-5
 
 
 def test_pool_up_trilinear(U):
