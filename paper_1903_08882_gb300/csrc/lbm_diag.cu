@@ -1,8 +1,9 @@
 // Diagnostic reductions: the global quantities of Secs. 3 and 4 from one
 // sample of node moments.
 //
-// Per node (FP32 from the FP32 moment arrays), summed per thread in FP32 with
-// Kahan compensation, then across threads and blocks in FP64:
+// Per node (FP32 from the FP32 moment arrays), summed per thread in FP32
+// (runs of at most 32 nodes, then the runs' sums), across a warp in
+// double-float (two FP32 words), then across warps and blocks in FP64:
 //   [0] 1                       [1] (rho - rho0)^2        [2] |u|^2
 //   [3] w^2                     [4] w T                   [5] 1/2 sum_ij (d_i u_j + d_j u_i)^2
 //   [6] |grad T|^2              [7] (div u)^2             [8+f] -dT/dn at Dirichlet face f
@@ -16,8 +17,9 @@
 // dT/dn = (-8 T_w + 9 T_0 - T_1)/3 with n pointing into the fluid.
 //
 // Reduction: warp shuffles, then shared memory, one FP64 partial per block
-// and quantity; a one-block kernel sums the partials in a fixed order, so a
-// sample is bit-reproducible for a given launch shape.
+// and quantity; a one-block kernel sums the partials in a fixed order.  The
+// wall terms go through shared FP64 atomics, so their last bits depend on
+// the order the warps add them.
 #include "lbm_device.cuh"
 #include "lbm_internal.h"
 
@@ -67,6 +69,31 @@ __device__ __forceinline__ void block_reduce(double (&v)[kNDiag], double (*sh)[k
     }
 }
 
+// Double-float value hi + lo (two FP32 words, about 48 significant bits).
+// FP64 arithmetic is slow on this GPU, so the warp stage of the reductions
+// adds these pairs with FP32 instructions (Knuth's error-free TwoSum, then a
+// renormalisation) and only the few per-warp results become FP64.
+struct DF {
+    float hi, lo;
+};
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    const float err = (a.hi - (s - bb)) + (b.hi - bb);
+    const float lo = a.lo + b.lo + err;
+    const float hi = s + lo;
+    return {hi, lo - (hi - s)};
+}
+__device__ __forceinline__ DF df_warp_sum(DF a) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const DF b = {__shfl_down_sync(0xffffffffu, a.hi, o), __shfl_down_sync(0xffffffffu, a.lo, o)};
+        a = df_add(a, b);
+    }
+    return a;
+}
+__device__ __forceinline__ double df_value(DF a) { return (double)a.hi + (double)a.lo; }
+
 struct WallT {
     float Tw[6];
 };
@@ -83,6 +110,7 @@ struct KSum {
         s = t;
     }
     __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+    __device__ __forceinline__ DF df() const { return {s, -c}; }
 };
 
 // Derivative from the values at the node and its two neighbours along an
@@ -99,24 +127,45 @@ __device__ __forceinline__ float dval(float pm, float p0, float pp, bool wm, boo
 // Diagnostic sums of one sample.  The lattice is cut into columns of
 // kDiagTX x kDiagTY nodes in x, y and segments of kDiagSeg planes in z; a
 // block takes one such brick at a time (bricks strided over the grid, so any
-// grid size works) and marches up its planes: each thread keeps the four
-// fields (u, v, w, T) of its own column at z - 1, z, z + 1 in registers for
-// the z derivatives, and the current plane goes through shared memory with
-// a one-node halo for the x and y derivatives.  Every field value is read
-// from memory about once (the halo and the two planes that start a segment
-// add ~15%).  Per-thread sums are compensated FP32 over at most kDiagSeg
-// nodes; the rare wall terms go into shared FP64 sums.
+// grid size works) and marches up its planes.  The planes of the brick (u,
+// v, w, T with a one-node halo in x and y for the derivatives, and
+// rho - rho0) stream through a ring of kDiagRing plane buffers in shared
+// memory: every thread copies its own column's values and its share of the
+// halo with 4-byte asynchronous copies (cp.async), kDiagAhead planes ahead
+// of the plane being reduced, so that the memory latency is covered by the
+// work on the planes in between, and one block barrier per plane publishes
+// a plane once all its copies have landed.  Every field value is read from
+// memory about once (the halo and the two planes that start a segment add
+// ~15%).  A warp whose nodes have no wall or wrap next to them takes plain
+// central differences.  Each thread sums its column of a brick (at most
+// kDiagSeg nodes) in FP32 and adds the column sums into FP32 totals (a few
+// dozen at most); the wall terms of a column (x and y faces) or of a
+// plane (z faces) go into shared FP64 sums.
 constexpr int kDiagTX = 32, kDiagTY = kDiagThreads / kDiagTX, kDiagSeg = 32;
+constexpr int kDiagAhead = 3;              // planes in flight beyond the three being read
+constexpr int kDiagRing = kDiagAhead + 4;  // the slot written at plane z was last read at plane z - 2
+struct DiagPlane {
+    float f[4][kDiagTY + 2][kDiagTX + 2]; // u, v, w, T with halo
+    float d[kDiagTY][kDiagTX];            // rho - rho0
+};
+
+__device__ __forceinline__ void cp4(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 __global__ void __launch_bounds__(kDiagThreads, 3) k_diag(const float *__restrict__ mom, Geom G, Phys P,
                                                        WallT W, double *__restrict__ partial) {
     __shared__ double sh[kDiagThreads / 32][kNDiag];
-    __shared__ float pl[4][kDiagTY + 2][kDiagTX + 2]; // u, v, w, T of the current plane, with halo
-    __shared__ double wall[12];                        // slots 8..13 and 18..23
+    __shared__ DiagPlane ring[kDiagRing];
+    __shared__ double wall[12]; // slots 8..13 and 18..23
     const int tx = threadIdx.x % kDiagTX, ty = threadIdx.x / kDiagTX;
     if (threadIdx.x < 12) wall[threadIdx.x] = 0.0;
-    KSum acc[10]; // slots 1..7, 14, 15 (acc[k] for slot k <= 7, acc[8] slot 14, acc[9] slot 15)
-    float vmax = 0.f;
+    float tot[9] = {}; // slots 1..7, 14, 15: sums of the thread's column sums
+    float umax2 = 0.f;
     uint32_t count = 0, bad = 0;
     const int64_t s = G.stride;
     const float *F[4] = {mom + s, mom + 2 * s, mom + 3 * s, mom + 4 * s};
@@ -127,6 +176,7 @@ __global__ void __launch_bounds__(kDiagThreads, 3) k_diag(const float *__restric
     const int nbricks = bx * by * bz;
     const bool dir[6] = {(P.dir_mask & 1) != 0, (P.dir_mask & 2) != 0, (P.dir_mask & 4) != 0,
                          (P.dir_mask & 8) != 0, (P.dir_mask & 16) != 0, (P.dir_mask & 32) != 0};
+    const bool anydir = P.dir_mask != 0;
     __syncthreads();
     for (int br = blockIdx.x; br < nbricks; br += gridDim.x) {
         const int ib = br % bx, jb = (br / bx) % by, kb = br / (bx * by);
@@ -134,7 +184,7 @@ __global__ void __launch_bounds__(kDiagThreads, 3) k_diag(const float *__restric
         const bool col = x < nx && y < ny;
         const int z0 = kb * kDiagSeg, z1 = min(nz, z0 + kDiagSeg);
         const uint32_t c = (uint32_t)(col ? x : 0) + (uint32_t)nx * (uint32_t)(col ? y : 0); // column offset
-        // halo cells this thread loads: row y - 1 or y + kDiagTY (hy), column
+        // halo cells this thread copies: row y - 1 or y + kDiagTY (hy), column
         // x - 1 or x + kDiagTX (hx), as flat in-plane offsets, -1 where none
         int64_t hy = -1, hx = -1;
         if (ty == 0 || ty == kDiagTY - 1) {
@@ -148,73 +198,94 @@ __global__ void __launch_bounds__(kDiagThreads, 3) k_diag(const float *__restric
             if (xw >= 0 && y < ny) hx = (int64_t)xw + (int64_t)nx * y;
         }
         const int ry = ty == 0 ? 0 : kDiagTY + 1, cx = tx == 0 ? 0 : kDiagTX + 1;
-        auto zwrap = [&](int zz) { return zz < nz ? zz : (perz ? zz - nz : nz - 1); };
-        // registers: the column's fields at z - 1 (pm), z (p0), z + 1 (pp), and the
-        // loads for the next plane in flight: z + 2 (pn), the halo of z + 1, rho of z + 1
-        float pm[4], p0[4], pp[4], pn[4], hyv[4], hxv[4];
-        float d0;
-        const int zb = z0 > 0 ? z0 - 1 : (perz ? nz - 1 : 0);
-        {
-            const uint32_t pb = G.nxy * (uint32_t)zb, p0z = G.nxy * (uint32_t)z0, p1 = G.nxy * (uint32_t)zwrap(z0 + 1);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                pm[q] = col ? F[q][c + pb] : 0.f;
-                p0[q] = col ? F[q][c + p0z] : 0.f;
-                pp[q] = col ? F[q][c + p1] : 0.f;
-                hyv[q] = hy >= 0 ? F[q][hy + p0z] : 0.f;
-                hxv[q] = hx >= 0 ? F[q][hx + p0z] : 0.f;
-            }
-            d0 = col ? dr[c + p0z] : 0.f;
-        }
-        for (int z = z0; z < z1; ++z) {
-            const bool zlo = z == 0 && !perz, zhi = z == nz - 1 && !perz;
-            const uint32_t plane = G.nxy * (uint32_t)z;
-            // the current plane into shared memory: own values, then the halo
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                pl[q][ty + 1][tx + 1] = p0[q];
-                if (ty == 0 || ty == kDiagTY - 1) pl[q][ry][tx + 1] = hyv[q];
-                if (tx == 0 || tx == kDiagTX - 1) pl[q][ty + 1][cx] = hxv[q];
-            }
-            // issue the next plane's loads now; they complete during this plane's work
-            const bool more = z + 1 < z1;
-            const uint32_t nplane = G.nxy * (uint32_t)zwrap(z + 1), n2 = G.nxy * (uint32_t)zwrap(z + 2);
-            float dn = 0.f;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                pn[q] = (more && col) ? F[q][c + n2] : 0.f;
-                hyv[q] = (more && hy >= 0) ? F[q][hy + nplane] : 0.f;
-                hxv[q] = (more && hx >= 0) ? F[q][hx + nplane] : 0.f;
-            }
-            if (more && col) dn = dr[c + nplane];
-            __syncthreads();
-            if (col) {
-                const uint32_t n = c + plane;
-                const bool xlo = x == 0 && !perx, xhi = x == nx - 1 && !perx;
-                const bool ylo = y == 0 && !pery, yhi = y == ny - 1 && !pery;
-                // neighbour values along x and y from the plane buffer; the last node of
-                // a periodic axis that ends inside the tile reads its wrapped neighbour
-                // (node 0 of the axis) from memory
-                const bool wrapx = perx && x == nx - 1 && tx < kDiagTX - 1;
-                const bool wrapy = pery && y == ny - 1 && ty < kDiagTY - 1;
-                float du[3][3], gT[3];
+        // the Dirichlet x and y faces this column lies on (-1: none; nx, ny >= 3,
+        // so at most one of each) and its wall terms summed over the brick
+        const int fxc = !col || perx ? -1 : (x == 0 && dir[0]) ? 0 : (x == nx - 1 && dir[1]) ? 1 : -1;
+        const int fyc = !col || pery ? -1 : (y == 0 && dir[2]) ? 2 : (y == ny - 1 && dir[3]) ? 3 : -1;
+        float wxa = 0.f, wxb = 0.f, wya = 0.f, wyb = 0.f;
+        // plane zz (z0 - 1 <= zz <= z1) of the brick into its ring slot; planes
+        // outside the lattice (no periodic wrap) are not copied and never read
+        auto issue = [&](int zz) {
+            const int za = zz < 0 ? (perz ? zz + nz : -1) : zz >= nz ? (perz ? zz - nz : -1) : zz;
+            if (zz <= z1 && za >= 0) {
+                DiagPlane &r = ring[(zz - z0 + 1) % kDiagRing];
+                const int64_t pz = (int64_t)G.nxy * za;
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const float xm = pl[q][ty + 1][tx];
-                    const float xp = wrapx ? F[q][(uint32_t)nx * (uint32_t)y + plane] : pl[q][ty + 1][tx + 2];
-                    const float ym = pl[q][ty][tx + 1];
-                    const float yp = wrapy ? F[q][(uint32_t)x + plane] : pl[q][ty + 2][tx + 1];
-                    if (q < 3) {
-                        du[0][q] = dval(xm, p0[q], xp, xlo, xhi, true, 0.f, true, 0.f);
-                        du[1][q] = dval(ym, p0[q], yp, ylo, yhi, true, 0.f, true, 0.f);
-                        du[2][q] = dval(pm[q], p0[q], pp[q], zlo, zhi, true, 0.f, true, 0.f);
-                    } else {
-                        gT[0] = dval(xm, p0[3], xp, xlo, xhi, dir[0], W.Tw[0], dir[1], W.Tw[1]);
-                        gT[1] = dval(ym, p0[3], yp, ylo, yhi, dir[2], W.Tw[2], dir[3], W.Tw[3]);
-                        gT[2] = dval(pm[3], p0[3], pp[3], zlo, zhi, dir[4], W.Tw[4], dir[5], W.Tw[5]);
+                    if (col) cp4(&r.f[q][ty + 1][tx + 1], F[q] + pz + c);
+                    if (hy >= 0) cp4(&r.f[q][ry][tx + 1], F[q] + pz + hy);
+                    if (hx >= 0) cp4(&r.f[q][ty + 1][cx], F[q] + pz + hx);
+                }
+                if (col) cp4(&r.d[ty][tx], dr + pz + c);
+            }
+            cp_commit(); // one group per plane, empty or not, so that the counts line up
+        };
+        for (int zz = z0 - 1; zz <= z0 + kDiagAhead; ++zz) issue(zz);
+        float bs[9]; // plain FP32 sums over the brick's column (at most kDiagSeg nodes)
+#pragma unroll
+        for (int k = 0; k < 9; ++k) bs[k] = 0.f;
+        for (int z = z0; z < z1; ++z) {
+            issue(z + 1 + kDiagAhead);
+            cp_wait<kDiagAhead>(); // this thread's copies of the planes up to z + 1
+            __syncthreads();       // ... and everyone's
+            const DiagPlane &Rm = ring[(z - z0) % kDiagRing], &R0 = ring[(z - z0 + 1) % kDiagRing],
+                            &Rp = ring[(z - z0 + 2) % kDiagRing];
+            const bool zlo = z == 0 && !perz, zhi = z == nz - 1 && !perz;
+            const uint32_t plane = G.nxy * (uint32_t)z;
+            float p0[4], pm[4], pp[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                p0[q] = R0.f[q][ty + 1][tx + 1];
+                pm[q] = Rm.f[q][ty + 1][tx + 1];
+                pp[q] = Rp.f[q][ty + 1][tx + 1];
+            }
+            const bool xlo = x == 0 && !perx, xhi = x == nx - 1 && !perx;
+            const bool ylo = y == 0 && !pery, yhi = y == ny - 1 && !pery;
+            // the last node of a periodic axis that ends inside the tile reads
+            // its wrapped neighbour (node 0 of the axis) from memory
+            const bool wrapx = perx && x == nx - 1 && tx < kDiagTX - 1;
+            const bool wrapy = pery && y == ny - 1 && ty < kDiagTY - 1;
+            // a warp with no wall and no wrap among its nodes takes central
+            // differences throughout
+            const bool plain = !col || !(xlo || xhi || ylo || yhi || zlo || zhi || wrapx || wrapy);
+            const bool fast = __all_sync(0xffffffffu, plain);
+            if (col) {
+                float du[3][3], gT[3];
+                if (fast) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float gx = 0.5f * (R0.f[q][ty + 1][tx + 2] - R0.f[q][ty + 1][tx]);
+                        const float gy = 0.5f * (R0.f[q][ty + 2][tx + 1] - R0.f[q][ty][tx + 1]);
+                        const float gz = 0.5f * (pp[q] - pm[q]);
+                        if (q < 3) {
+                            du[0][q] = gx;
+                            du[1][q] = gy;
+                            du[2][q] = gz;
+                        } else {
+                            gT[0] = gx;
+                            gT[1] = gy;
+                            gT[2] = gz;
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const float xm = R0.f[q][ty + 1][tx];
+                        const float xp = wrapx ? F[q][(uint32_t)nx * (uint32_t)y + plane] : R0.f[q][ty + 1][tx + 2];
+                        const float ym = R0.f[q][ty][tx + 1];
+                        const float yp = wrapy ? F[q][(uint32_t)x + plane] : R0.f[q][ty + 2][tx + 1];
+                        if (q < 3) {
+                            du[0][q] = dval(xm, p0[q], xp, xlo, xhi, true, 0.f, true, 0.f);
+                            du[1][q] = dval(ym, p0[q], yp, ylo, yhi, true, 0.f, true, 0.f);
+                            du[2][q] = dval(pm[q], p0[q], pp[q], zlo, zhi, true, 0.f, true, 0.f);
+                        } else {
+                            gT[0] = dval(xm, p0[3], xp, xlo, xhi, dir[0], W.Tw[0], dir[1], W.Tw[1]);
+                            gT[1] = dval(ym, p0[3], yp, ylo, yhi, dir[2], W.Tw[2], dir[3], W.Tw[3]);
+                            gT[2] = dval(pm[3], p0[3], pp[3], zlo, zhi, dir[4], W.Tw[4], dir[5], W.Tw[5]);
+                        }
                     }
                 }
-                const float d = d0, u = p0[0], vv = p0[1], w = p0[2], t = p0[3];
+                const float d = R0.d[ty][tx], u = p0[0], vv = p0[1], w = p0[2], t = p0[3];
                 const float uu = u * u + vv * vv + w * w;
                 float eps = 0.f;
 #pragma unroll
@@ -226,61 +297,109 @@ __global__ void __launch_bounds__(kDiagThreads, 3) k_diag(const float *__restric
                     }
                 const float dv = du[0][0] + du[1][1] + du[2][2];
                 count += 1;
-                acc[1].add(d * d);
-                acc[2].add(uu);
-                acc[3].add(w * w);
-                acc[4].add(w * t);
-                acc[5].add(eps);
-                acc[6].add(gT[0] * gT[0] + gT[1] * gT[1] + gT[2] * gT[2]);
-                acc[7].add(dv * dv);
-                acc[8].add(t);
-                acc[9].add(d); // sum rho = nodes + sum (rho - rho0)
-                vmax = fmaxf(vmax, sqrtf(uu));
-                if (!isfinite(uu) || !isfinite(t) || !isfinite(d)) bad += 1;
-                // Dirichlet faces: wall gradient and anti-bounce-back link flux
-                const bool at[6] = {xlo, xhi, ylo, yhi, zlo, zhi};
-#pragma unroll
-                for (int fc = 0; fc < 6; ++fc) {
-                    if (!at[fc] || !dir[fc]) continue;
-                    const int a = fc / 2;
-                    const float t1 = a == 0 ? pl[3][ty + 1][fc == 0 ? tx + 2 : tx]
-                                   : a == 1 ? pl[3][fc == 2 ? ty + 2 : ty][tx + 1]
-                                            : (fc == 4 ? pp[3] : pm[3]);
-                    const float dTdn = (-8.f * W.Tw[fc] + 9.f * t - t1) * (1.f / 3.f);
-                    atomicAdd(&wall[fc], (double)(-dTdn));
-                    const float gin = mom[(5 + fc) * s + n];
-                    atomicAdd(&wall[6 + fc], (double)(2.f * gin - P.abbT[fc]));
+                bs[0] += d * d;
+                bs[1] += uu;
+                bs[2] += w * w;
+                bs[3] += w * t;
+                bs[4] += eps;
+                bs[5] += gT[0] * gT[0] + gT[1] * gT[1] + gT[2] * gT[2];
+                bs[6] += dv * dv;
+                bs[7] += t;
+                bs[8] += d; // sum rho = nodes + sum (rho - rho0)
+                umax2 = fmaxf(umax2, uu);
+                if (!(fabsf(uu) + fabsf(t) + fabsf(d) < INFINITY)) bad += 1; // a NaN or infinite moment
+            }
+            // Dirichlet faces: wall gradient -dT/dn (from the node and the next
+            // one inward) and anti-bounce-back link flux 2 g_in - (6 + a_T)/21 T_w;
+            // x and y faces summed per column, z faces (a whole plane) per warp
+            if (!anydir || fast) continue; // no face node in this warp
+            // (constant-index selects keep the wall tables out of local memory)
+            if (fxc >= 0) {
+                const bool lo = fxc == 0;
+                const float t1 = R0.f[3][ty + 1][lo ? tx + 2 : tx];
+                wxa += (8.f * (lo ? W.Tw[0] : W.Tw[1]) - 9.f * p0[3] + t1) * (1.f / 3.f);
+                wxb += 2.f * mom[(5 + fxc) * s + c + plane] - (lo ? P.abbT[0] : P.abbT[1]);
+            }
+            if (fyc >= 0) {
+                const bool lo = fyc == 2;
+                const float t1 = R0.f[3][lo ? ty + 2 : ty][tx + 1];
+                wya += (8.f * (lo ? W.Tw[2] : W.Tw[3]) - 9.f * p0[3] + t1) * (1.f / 3.f);
+                wyb += 2.f * mom[(5 + fyc) * s + c + plane] - (lo ? P.abbT[2] : P.abbT[3]);
+            }
+            const int fzc = perz ? -1 : (zlo && dir[4]) ? 4 : (zhi && dir[5]) ? 5 : -1; // uniform
+            if (fzc >= 0) {
+                const bool lo = fzc == 4;
+                float ta = 0.f, tb = 0.f;
+                if (col) {
+                    ta = (8.f * (lo ? W.Tw[4] : W.Tw[5]) - 9.f * p0[3] + (lo ? pp[3] : pm[3])) * (1.f / 3.f);
+                    tb = 2.f * mom[(5 + fzc) * s + c + plane] - (lo ? P.abbT[4] : P.abbT[5]);
+                }
+                const DF da = df_warp_sum({ta, 0.f}), db = df_warp_sum({tb, 0.f});
+                if ((threadIdx.x & 31) == 0) {
+                    atomicAdd(&wall[fzc], df_value(da));
+                    atomicAdd(&wall[6 + fzc], df_value(db));
                 }
             }
-            __syncthreads(); // the plane buffer is rewritten next
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                pm[q] = p0[q];
-                p0[q] = pp[q];
-                pp[q] = pn[q];
-            }
-            d0 = dn;
         }
+        // the column's sums into the thread's totals; its x and y wall terms
+        // into the shared FP64 sums
+#pragma unroll
+        for (int k = 0; k < 9; ++k) tot[k] += bs[k];
+        if (fxc >= 0) {
+            atomicAdd(&wall[fxc], (double)wxa);
+            atomicAdd(&wall[6 + fxc], (double)wxb);
+        }
+        if (fyc >= 0) {
+            atomicAdd(&wall[fyc], (double)wya);
+            atomicAdd(&wall[6 + fyc], (double)wyb);
+        }
+        cp_wait<0>();
+        __syncthreads(); // the ring is refilled by the next brick
     }
-    double v[kNDiag];
+    const float vmax = sqrtf(umax2);
+    // block reduction: double-float warp sums, FP64 across the warps
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    constexpr int slot[10] = {0, 1, 2, 3, 4, 5, 6, 7, 14, 15};
 #pragma unroll
-    for (int k = 0; k < kNDiag; ++k) v[k] = 0.0;
+    for (int k = 1; k < 10; ++k) {
+        const DF r = df_warp_sum({tot[k - 1], 0.f});
+        if (lane == 0) sh[wid][slot[k]] = df_value(r);
+    }
+    count = __reduce_add_sync(0xffffffffu, count);
+    bad = __reduce_add_sync(0xffffffffu, bad);
+    float vm = vmax;
 #pragma unroll
-    for (int k = 1; k <= 7; ++k) v[k] = acc[k].value();
-    v[14] = acc[8].value();
-    v[0] = (double)count;
-    v[15] = acc[9].value() + (double)count;
-    v[16] = (double)vmax;
-    v[17] = (double)bad;
-    block_reduce(v, sh);
-    if (threadIdx.x == 0) {
+    for (int o = 16; o > 0; o >>= 1) vm = fmaxf(vm, __shfl_down_sync(0xffffffffu, vm, o));
+    if (lane == 0) {
+        sh[wid][0] = (double)count;
+        sh[wid][15] += (double)count; // sum rho = nodes + sum (rho - rho0)
+        sh[wid][16] = (double)vm;
+        sh[wid][17] = (double)bad;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        double v[kNDiag];
+        constexpr int nw = kDiagThreads / 32;
 #pragma unroll
-        for (int fc = 0; fc < 6; ++fc) {
-            v[8 + fc] = wall[fc];
-            v[18 + fc] = wall[6 + fc];
+        for (int k = 0; k < kNDiag; ++k) {
+            if ((k >= 8 && k <= 13) || k >= 18) continue; // wall slots: below
+            double r = lane < nw ? sh[lane][k] : 0.0;
+#pragma unroll
+            for (int o = nw / 2; o > 0; o >>= 1) {
+                const double t = __shfl_down_sync(0xffffffffu, r, o);
+                r = k == 16 ? fmax(r, t) : r + t;
+            }
+            v[k] = r;
         }
+        if (lane == 0) {
 #pragma unroll
-        for (int k = 0; k < kNDiag; ++k) partial[(int64_t)blockIdx.x * kNDiag + k] = v[k];
+            for (int fc = 0; fc < 6; ++fc) {
+                v[8 + fc] = wall[fc];
+                v[18 + fc] = wall[6 + fc];
+            }
+#pragma unroll
+            for (int k = 0; k < kNDiag; ++k) partial[(int64_t)blockIdx.x * kNDiag + k] = v[k];
+        }
     }
 }
 
@@ -341,32 +460,32 @@ __device__ __forceinline__ void local_eps(const float *__restrict__ mom, int64_t
 }
 
 // Pass 1 of the dissipation PDFs: sums of eps_u^2 and eps_T^2 over the nodes
-// (FP64), one atomic add per block and quantity into sums[0..1].
+// (compensated FP32 per thread, double-float across the warp, FP64 across
+// warps), one atomic add per block and quantity into sums[0..1].
 __global__ void __launch_bounds__(kDiagThreads) k_eps_sq(const float *__restrict__ mom, Geom G, Phys P,
                                                          WallT W, float nu, float ka,
                                                          double *__restrict__ sums) {
     __shared__ double sh[kDiagThreads / 32][2];
-    double a0 = 0.0, a1 = 0.0;
+    KSum a0, a1;
     for (uint32_t n = blockIdx.x * blockDim.x + threadIdx.x; n < G.n; n += gridDim.x * blockDim.x) {
         float eu, et;
         local_eps(mom, G.stride, G, P, W, n, nu, ka, eu, et);
-        a0 += (double)eu * (double)eu;
-        a1 += (double)et * (double)et;
+        a0.add(eu * eu);
+        a1.add(et * et);
     }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    a0 = warp_sum(a0);
-    a1 = warp_sum(a1);
+    const DF r0 = df_warp_sum(a0.df()), r1 = df_warp_sum(a1.df());
     if (lane == 0) {
-        sh[wid][0] = a0;
-        sh[wid][1] = a1;
+        sh[wid][0] = df_value(r0);
+        sh[wid][1] = df_value(r1);
     }
     __syncthreads();
     if (wid == 0) {
-        a0 = warp_sum(lane < nw ? sh[lane][0] : 0.0);
-        a1 = warp_sum(lane < nw ? sh[lane][1] : 0.0);
+        const double b0 = warp_sum(lane < nw ? sh[lane][0] : 0.0);
+        const double b1 = warp_sum(lane < nw ? sh[lane][1] : 0.0);
         if (lane == 0) {
-            atomicAdd(&sums[0], a0);
-            atomicAdd(&sums[1], a1);
+            atomicAdd(&sums[0], b0);
+            atomicAdd(&sums[1], b1);
         }
     }
 }
@@ -523,16 +642,19 @@ cudaError_t launch_nu_profile(const float *mom, const Geom &G, const Phys &P, co
 }
 
 int diag_blocks(const Geom &G) {
-    // bricks of the diagnostics kernel, at most 8 blocks per SM of the current device
+    // one brick per block at most, and no more blocks than the device holds
+    // at once (k_diag's occupancy times the SM count), so that the bricks are
+    // shared out in a single wave and each block reduces its sums once
     const int64_t need = (int64_t)((G.nx + kDiagTX - 1) / kDiagTX) * ((G.ny + kDiagTY - 1) / kDiagTY) *
                          ((G.nz + kDiagSeg - 1) / kDiagSeg);
-    int dev = 0, nsm = 0;
+    int dev = 0, nsm = 0, per = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) !=
-                                                  cudaSuccess || nsm < 1) {
-        cudaGetLastError();
+                                                  cudaSuccess || nsm < 1)
         nsm = 152;
-    }
-    const int64_t cap = 8 * (int64_t)nsm;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_diag, kDiagThreads, 0) != cudaSuccess || per < 1)
+        per = 3;
+    cudaGetLastError();
+    const int64_t cap = (int64_t)per * nsm;
     return (int)(need < cap ? need : cap);
 }
 
