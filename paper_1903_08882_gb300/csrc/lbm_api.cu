@@ -443,6 +443,7 @@ lbm_status lbm_create(const lbm_params *params, const lbm_allocator *alloc, void
             T.grid = nsm * per_sm; // persistent: every block resident
             T.xf = G.nx >= staged_xf_min_nx() ? 1 : 0;
             T.budget = 1ll << 31;
+            staged_store_offsets(params->storage, G, T);
             ctx->staged = true;
         }
         cudaGetLastError(); // a failed opt-in leaves the register kernels in use

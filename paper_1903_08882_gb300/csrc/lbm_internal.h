@@ -22,6 +22,9 @@ struct StagedGeom {
     int grid;            // persistent blocks
     int xf;              // 1: the odd kernel updates the x-face nodes of its rows (nx >= staged_xf_min_nx())
     long long budget;    // clock cycles one pipeline wait may take
+    // odd step: byte offset, from the f (q < 19) or g array base, of the slot
+    // a node's population q streams to: array q at the node + e_q
+    long long soff[26];
 };
 
 struct StepArgs {
@@ -55,6 +58,8 @@ cudaError_t staged_prepare(int storage, int *blocks_per_sm);
 int staged_smem_bytes(int storage);
 int staged_tile_nodes();
 int staged_xf_min_nx();
+// Fills T.soff for the storage format and lattice.
+void staged_store_offsets(int storage, const Geom &G, StagedGeom &T);
 // op 0: staging -> device layout, 1: device layout -> staging, 2: moments -> st
 cudaError_t launch_convert(int storage, int op, float *st, void *f, void *g, const Geom &G,
                            const Phys &P, int layout, cudaStream_t stream);

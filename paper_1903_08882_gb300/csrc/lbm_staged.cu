@@ -50,7 +50,8 @@ namespace {
 constexpr int kThreads = 256;           // threads per block
 constexpr int kTile = 2 * kThreads;     // nodes per tile
 constexpr int kSlack = 32;              // window bytes beyond the tile: 16-byte rounding at both ends
-constexpr int kHead = 1024;             // shared-memory header: mbarriers and window shifts
+constexpr int kHead = 1024;             // shared-memory header: mbarriers and window offsets
+constexpr int kWofs = 28;               // window offsets per stage (26, padded for 16-byte loads)
 constexpr long long kDrain = 1ll << 31; // cycles to wait for copies in flight before leaving after a timeout
 // In-tile x faces: a tile of kTile consecutive nodes touches at most
 // kXfRows rows of at least kXfMinNx nodes; each row has two x-face nodes and
@@ -184,9 +185,10 @@ template <bool ODD> __device__ __forceinline__ TileSpan tile_span(const Geom &G,
 }
 
 // Copy one tile into a stage.  Called by all 32 lanes of one warp.
-// Lane q < 26 computes and issues window q: shift[q] receives
-// n0 - off_q - (first element copied), so that node n0 + j of the tile sits
-// at element j + shift[q] of window q.
+// Lane q < 26 computes and issues window q: wofs[q] receives the byte offset
+// in the stage of the element that node n0 of the tile reads, so that node
+// n0 + j reads element j from there (the window starts n0 - off_q - (first
+// element copied) elements before it).
 // XF (odd step, rows of at least kXfMinNx nodes): the values that arrive at
 // the tile's x-face nodes through their face are not in the windows (they
 // come from the node's own slot at a wall, or from the far end of the row
@@ -197,7 +199,7 @@ template <bool ODD> __device__ __forceinline__ TileSpan tile_span(const Geom &G,
 // the same barrier.
 template <int S, bool ODD, bool XF>
 __device__ __forceinline__ void issue_tile(const SF<S> *f, const SG<S> *g, const Geom &G, const TileSpan &sp,
-                                           unsigned char *stage, int *shift, uint64_t *bar, int lane) {
+                                           unsigned char *stage, int *wofs, uint64_t *bar, int lane) {
     unsigned sz = 0;
     const char *src = nullptr;
     if (lane < 26) {
@@ -210,7 +212,7 @@ __device__ __forceinline__ void issue_tile(const SF<S> *f, const SG<S> *g, const
         a = a < 0 ? 0 : a;
         b = b > lim ? lim : b;
         sz = b > a ? (unsigned)(b - a) : 0u;
-        shift[q] = (int)(first - a / es);
+        wofs[q] = Stage<S>::offset(q) + (int)((first - a / es) * es);
         const int arr = ODD ? src_array(q) : q;
         src = (arr < 19 ? reinterpret_cast<const char *>(f + (int64_t)arr * G.stride)
                         : reinterpret_cast<const char *>(g + (int64_t)(arr - 19) * G.stride)) + a;
@@ -304,7 +306,7 @@ __global__ void __launch_bounds__(kThreads, 2)
     constexpr int NST = Stage<S>::count;
     extern __shared__ __align__(1024) unsigned char smem[];
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
-    int *shift = reinterpret_cast<int *>(smem + 64); // [NST][26]
+    int *wofs = reinterpret_cast<int *>(smem + 64); // [NST][kWofs]: window offsets of each stage
     unsigned char *stages = smem + kHead;
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
@@ -322,7 +324,7 @@ __global__ void __launch_bounds__(kThreads, 2)
             const uint32_t t = blockIdx.x + (uint32_t)k * gridDim.x;
             if (t < ntiles)
                 issue_tile<S, ODD, XF>(f, g, G, tile_span<ODD>(G, T, t), stages + k * Stage<S>::bytes,
-                                       shift + 26 * k, &bar[k], lane);
+                                       wofs + kWofs * k, &bar[k], lane);
         }
     }
 
@@ -342,8 +344,13 @@ __global__ void __launch_bounds__(kThreads, 2)
         if (ODD) {
             const uint32_t nx = (uint32_t)G.nx;
             r0 = fast_div(m, G.mag_nx);
-            r1 = fast_div(mb, G.mag_nx);
-            const uint32_t xa = m - nx * r0, xb = mb - nx * r1;
+            const uint32_t xa = m - nx * r0;
+            // mb = m + 32 lies at most 32 / nx rows further (two for nx >= 16)
+            uint32_t xb = xa + 32u;
+            r1 = r0;
+            if (xb >= nx) { xb -= nx; ++r1; }
+            if (xb >= nx) { xb -= nx; ++r1; }
+            if (nx < 16u) { r1 = fast_div(mb, G.mag_nx); xb = mb - nx * r1; }
             if (XF) {
                 lo0 = v0 && xa == 0u;
                 hi0 = v0 && xa == nx - 1u;
@@ -358,11 +365,10 @@ __global__ void __launch_bounds__(kThreads, 2)
         const bool ok = mbar_wait(&bar[st], parity, T.budget);
         if (ok && (v0 || v1)) {
             const unsigned char *sb = stages + st * Stage<S>::bytes;
-            const int *sh = shift + 26 * st;
             float2 fl[19], gl[7];
             if (!ODD) {
                 // even tiles start on a 1024-byte boundary of every array, so the
-                // windows are not shifted (shift[q] = 0)
+                // windows are not shifted
 #pragma unroll
                 for (int q = 0; q < 19; ++q)
                     fl[q] = PF<S>::ld(reinterpret_cast<const SF<S> *>(sb + Stage<S>::offset(q)) + o);
@@ -370,14 +376,26 @@ __global__ void __launch_bounds__(kThreads, 2)
                 for (int q = 0; q < 7; ++q)
                     gl[q] = PG<S>::ld(reinterpret_cast<const SG<S> *>(sb + Stage<S>::offset(19 + q)) + o);
             } else {
+                // the stage's window offsets, four per 16-byte load
+                int wo[kWofs];
+                const int4 *w4 = reinterpret_cast<const int4 *>(wofs + kWofs * st);
+#pragma unroll
+                for (int k = 0; k < kWofs / 4; ++k) {
+                    const int4 v = w4[k];
+                    wo[4 * k] = v.x;
+                    wo[4 * k + 1] = v.y;
+                    wo[4 * k + 2] = v.z;
+                    wo[4 * k + 3] = v.w;
+                }
+                const unsigned char *bf = sb + sizeof(SF<S>) * o, *bg = sb + sizeof(SG<S>) * o;
 #pragma unroll
                 for (int q = 0; q < 19; ++q) {
-                    const SF<S> *w = reinterpret_cast<const SF<S> *>(sb + Stage<S>::offset(q)) + o + sh[q];
+                    const SF<S> *w = reinterpret_cast<const SF<S> *>(bf + wo[q]);
                     fl[q] = make_float2(PF<S>::one(w[0]), PF<S>::one(w[32]));
                 }
 #pragma unroll
                 for (int q = 0; q < 7; ++q) {
-                    const SG<S> *w = reinterpret_cast<const SG<S> *>(sb + Stage<S>::offset(19 + q)) + o + sh[19 + q];
+                    const SG<S> *w = reinterpret_cast<const SG<S> *>(bg + wo[19 + q]);
                     gl[q] = make_float2(PG<S>::one(w[0]), PG<S>::one(w[32]));
                 }
                 if (XF && (lo0 || hi0 || lo1 || hi1)) {
@@ -407,9 +425,12 @@ __global__ void __launch_bounds__(kThreads, 2)
             } else {
                 // a link that leaves an x-face node through its face is stored below instead
                 const bool p0 = v0 && !hi0, m0 = v0 && !lo0, p1 = v1 && !hi1, m1 = v1 && !lo1;
+                // destination: array q at the node + e_q, a byte offset per q from
+                // the node's own element
+                const char *fm = reinterpret_cast<const char *>(fo + m), *gm = reinterpret_cast<const char *>(go + m);
 #pragma unroll
                 for (int q = 0; q < 19; ++q) {
-                    SF<S> *p = fo + q * s + (int64_t)m + G.off[q];
+                    SF<S> *p = reinterpret_cast<SF<S> *>(const_cast<char *>(fm) + T.soff[q]);
                     const bool c0 = ex19(q) > 0 ? p0 : ex19(q) < 0 ? m0 : v0;
                     const bool c1 = ex19(q) > 0 ? p1 : ex19(q) < 0 ? m1 : v1;
                     if (c0) PF<S>::st1(p, fl[q].x);
@@ -418,7 +439,7 @@ __global__ void __launch_bounds__(kThreads, 2)
                 const uint32_t rb0 = SRG(S) ? rnd_node(m, P.t) : 0u, rb1 = SRG(S) ? rnd_node(mb, P.t) : 0u;
 #pragma unroll
                 for (int q = 0; q < 7; ++q) {
-                    SG<S> *p = go + q * s + (int64_t)m + G.off[q];
+                    SG<S> *p = reinterpret_cast<SG<S> *>(const_cast<char *>(gm) + T.soff[19 + q]);
                     const bool c0 = ex7(q) > 0 ? p0 : ex7(q) < 0 ? m0 : v0;
                     const bool c1 = ex7(q) > 0 ? p1 : ex7(q) < 0 ? m1 : v1;
                     if (c0) PG<S>::st1s(p, gl[q].x, rnd_pop(rb0, q));
@@ -449,7 +470,7 @@ __global__ void __launch_bounds__(kThreads, 2)
             const uint32_t tn = t + (uint32_t)NST * gridDim.x;
             if (tn < ntiles)
                 issue_tile<S, ODD, XF>(f, g, G, tile_span<ODD>(G, T, tn), stages + st * Stage<S>::bytes,
-                                       shift + 26 * st, &bar[st], lane);
+                                       wofs + kWofs * st, &bar[st], lane);
         }
     }
 }
@@ -504,6 +525,12 @@ int staged_smem_bytes(int storage) {
 int staged_tile_nodes() { return kTile; }
 
 int staged_xf_min_nx() { return kXfMinNx; }
+
+void staged_store_offsets(int storage, const Geom &G, StagedGeom &T) {
+    const int64_t ef = storage == ST_F32 ? 4 : 2, eg = (storage == ST_F32 || storage == ST_F16M) ? 4 : 2;
+    for (int q = 0; q < 19; ++q) T.soff[q] = (q * G.stride + G.off[q]) * ef;
+    for (int q = 0; q < 7; ++q) T.soff[19 + q] = (q * G.stride + G.off[q]) * eg;
+}
 
 cudaError_t staged_prepare(int storage, int *blocks_per_sm) {
     switch (storage) {
