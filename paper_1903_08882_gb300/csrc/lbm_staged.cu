@@ -248,54 +248,64 @@ __device__ __forceinline__ void issue_tile(const SF<S> *f, const SG<S> *g, const
     }
 }
 
-// x-face node (side 0: x = 0, side 1: x = nx-1) of component K of a pair:
+// x-face node (hi = false: x = 0, true: x = nx-1) of component K of a pair:
 // the links that arrive through its face take the fetched words (w: the
-// node's six words), with anti-bounce-back for g at a Dirichlet face.
-template <int S, int SIDE, int K>
-__device__ __forceinline__ void xface_in(float2 (&fl)[19], float2 (&gl)[7], const uint32_t *w, uint32_t n,
+// node's six words), with anti-bounce-back for g at a Dirichlet face.  The
+// side is a per-lane value, so that the lanes holding the two ends of a row
+// run this once together.
+template <int K> __device__ __forceinline__ void set_k(float2 &d, float v) {
+    if (K == 0) d.x = v;
+    else d.y = v;
+}
+template <int S, int K>
+__device__ __forceinline__ void xface_in(float2 (&fl)[19], float2 (&gl)[7], const uint32_t *w, uint32_t n, bool hi,
                                          const Geom &G, const Phys &P) {
     const bool per = G.periodic & 1;
-    const int64_t wrap = SIDE ? -(int64_t)G.nx : (int64_t)G.nx;
+    const int64_t wrap = hi ? -(int64_t)G.nx : (int64_t)G.nx;
 #pragma unroll
     for (int j = 0; j < 5; ++j) {
-        const int q = xlink(SIDE, j);
-        const uint32_t at = per ? (uint32_t)((int64_t)n - G.off[q] + wrap) : n;
+        const int q0 = xlink(0, j), q1 = xlink(1, j);
+        const int oq = hi ? G.off[q1] : G.off[q0];
+        const uint32_t at = per ? (uint32_t)((int64_t)n - oq + wrap) : n;
         const float v = PF<S>::word(w[j], at & 1u);
-        if (K == 0) fl[q].x = v;
-        else fl[q].y = v;
+        if (hi) set_k<K>(fl[q1], v);
+        else set_k<K>(fl[q0], v);
     }
-    const int q = 1 + SIDE;
-    const uint32_t at = per ? (uint32_t)((int64_t)n - G.off[q] + wrap) : n;
+    const int oq = hi ? G.off[2] : G.off[1];
+    const uint32_t at = per ? (uint32_t)((int64_t)n - oq + wrap) : n;
     float v = PG<S>::word(w[5], at & 1u);
-    if (!per && ((P.dir_mask >> SIDE) & 1)) v = P.abbT[SIDE] - v; // the link comes through face SIDE
-    if (K == 0) gl[q].x = v;
-    else gl[q].y = v;
+    if (!per && ((P.dir_mask >> (hi ? 1 : 0)) & 1)) v = (hi ? P.abbT[1] : P.abbT[0]) - v; // through the face
+    if (hi) set_k<K>(gl[2], v);
+    else set_k<K>(gl[1], v);
 }
 
 // The links that leave an x-face node through its face: bounce-back into the
 // node's own opposite slot (anti-bounce-back for g at a Dirichlet face), or
 // the far end of the row when x is periodic.
-template <int S, int SIDE, int K>
+template <int S, int K>
 __device__ __forceinline__ void xface_out(SF<S> *f, SG<S> *g, const float2 (&fl)[19], const float2 (&gl)[7],
-                                          uint32_t n, uint32_t rb, const Geom &G, const Phys &P) {
+                                          uint32_t n, uint32_t rb, bool hi, const Geom &G, const Phys &P) {
     const bool per = G.periodic & 1;
     const int64_t s = G.stride;
-    const int64_t wrap = SIDE ? (int64_t)G.nx : -(int64_t)G.nx; // side 0 leaves along -x
+    const int64_t wrap = hi ? (int64_t)G.nx : -(int64_t)G.nx; // x = 0 leaves along -x
 #pragma unroll
     for (int j = 0; j < 5; ++j) {
-        const int q = xlink(1 - SIDE, j); // e_x = -1 at x = 0, +1 at x = nx-1
-        const float v = K == 0 ? fl[q].x : fl[q].y;
-        SF<S> *p = per ? f + q * s + ((int64_t)n + G.off[q] - wrap) : f + opp19(q) * s + n;
+        const int qa = xlink(1, j), qb = xlink(0, j); // e_x = -1 at x = 0, +1 at x = nx-1
+        const float2 u = hi ? fl[qb] : fl[qa];
+        const float v = K == 0 ? u.x : u.y;
+        SF<S> *p = per ? f + (hi ? qb : qa) * s + ((int64_t)n + (hi ? G.off[qb] : G.off[qa]) - wrap)
+                       : f + (hi ? opp19(qb) : opp19(qa)) * s + n;
         PF<S>::st1(p, v);
     }
-    const int q = 2 - SIDE;
-    float v = K == 0 ? gl[q].x : gl[q].y;
+    const int q = hi ? 1 : 2;
+    const float2 u = hi ? gl[1] : gl[2];
+    float v = K == 0 ? u.x : u.y;
     SG<S> *p;
     if (per) {
-        p = g + q * s + ((int64_t)n + G.off[q] - wrap);
+        p = g + q * s + ((int64_t)n + (hi ? G.off[1] : G.off[2]) - wrap);
     } else {
-        p = g + opp7(q) * s + n;
-        if ((P.dir_mask >> SIDE) & 1) v = P.abbT[SIDE] - v; // the link leaves through face SIDE
+        p = g + (hi ? 2 : 1) * s + n; // the opposite slot
+        if ((P.dir_mask >> (hi ? 1 : 0)) & 1) v = (hi ? P.abbT[1] : P.abbT[0]) - v; // leaves through the face
     }
     PG<S>::st1s(p, v, rnd_pop(rb, q));
 }
@@ -401,10 +411,8 @@ __global__ void __launch_bounds__(kThreads, 2)
                 if (XF && (lo0 || hi0 || lo1 || hi1)) {
                     const uint32_t *side = reinterpret_cast<const uint32_t *>(sb + Stage<S>::win);
                     const uint32_t row0 = fast_div(sp.n0, G.mag_nx);
-                    if (lo0) xface_in<S, 0, 0>(fl, gl, side + 12u * (r0 - row0), m, G, P);
-                    if (hi0) xface_in<S, 1, 0>(fl, gl, side + 12u * (r0 - row0) + 6u, m, G, P);
-                    if (lo1) xface_in<S, 0, 1>(fl, gl, side + 12u * (r1 - row0), mb, G, P);
-                    if (hi1) xface_in<S, 1, 1>(fl, gl, side + 12u * (r1 - row0) + 6u, mb, G, P);
+                    if (lo0 || hi0) xface_in<S, 0>(fl, gl, side + 12u * (r0 - row0) + (hi0 ? 6u : 0u), m, hi0, G, P);
+                    if (lo1 || hi1) xface_in<S, 1>(fl, gl, side + 12u * (r1 - row0) + (hi1 ? 6u : 0u), mb, hi1, G, P);
                 }
             }
             collide(P, fl, gl);
@@ -446,10 +454,8 @@ __global__ void __launch_bounds__(kThreads, 2)
                     if (c1) PG<S>::st1s(p + 32, gl[q].y, rnd_pop(rb1, q));
                 }
                 if (XF && (lo0 || hi0 || lo1 || hi1)) {
-                    if (lo0) xface_out<S, 0, 0>(fo, go, fl, gl, m, rb0, G, P);
-                    if (hi0) xface_out<S, 1, 0>(fo, go, fl, gl, m, rb0, G, P);
-                    if (lo1) xface_out<S, 0, 1>(fo, go, fl, gl, mb, rb1, G, P);
-                    if (hi1) xface_out<S, 1, 1>(fo, go, fl, gl, mb, rb1, G, P);
+                    if (lo0 || hi0) xface_out<S, 0>(fo, go, fl, gl, m, rb0, hi0, G, P);
+                    if (lo1 || hi1) xface_out<S, 1>(fo, go, fl, gl, mb, rb1, hi1, G, P);
                 }
             }
         }
