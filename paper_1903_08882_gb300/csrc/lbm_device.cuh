@@ -372,7 +372,9 @@ __host__ __device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) {
     return make_float2(fmaf(a.x, b.x, c.x), fmaf(a.y, b.y, c.y));
 #endif
 }
+__host__ __device__ __forceinline__ double vfma(double a, double b, double c) { return fma(a, b, c); }
 __host__ __device__ __forceinline__ float vsplat(float a, float) { return a; }
+__host__ __device__ __forceinline__ double vsplat(float a, double) { return a; }
 __host__ __device__ __forceinline__ float2 vsplat(float a, float2) { return make_float2(a, a); }
 // correctly rounded reciprocal
 __host__ __device__ __forceinline__ float vrcp(float a) {
@@ -383,6 +385,7 @@ __host__ __device__ __forceinline__ float vrcp(float a) {
 #endif
 }
 __host__ __device__ __forceinline__ float2 vrcp(float2 a) { return make_float2(vrcp(a.x), vrcp(a.y)); }
+__host__ __device__ __forceinline__ double vrcp(double a) { return 1.0 / a; }
 
 // ------------------------------------------------------------- collision ----
 //
@@ -435,106 +438,97 @@ __host__ __device__ __forceinline__ MacroT<V> macro(const Phys &P, const V (&f)[
 // V = float2), in place:
 //   f+ = f - M^-1 [S (m - m^eq) - (I - S/2) M F~]      (Eq. MRT)
 //   g+ = g - N^-1 Q (n - n^eq)                          (Eq. MRT_T)
-// f holds deviations f - w rho0; the rest-state moments M w rho0 =
-// (rho0, -11 rho0, 3 rho0, 0, ...) are folded into m - m^eq below.
-// M^-1 = M^T diag(1/|M_k|^2), N^-1 = N^T diag(1/|N_k|^2).
+// With the rates of Sec. 2.2 (s_e = s_eps = s_nu = s_pi, s_q = s_m) S takes
+// one value s_e on the even non-conserved moments and one value s_q on the odd
+// ones; m^eq is M times the quadratic equilibrium
+//   f_i^eq = w_i rho (1 + 3 c.u + 9/2 (c.u)^2 - 3/2 u.u)
+// and M F~ is M times the forcing term
+//   F_i = w_i (3 (c - u).F + 9 (c.u)(c.F)),
+// and the rows of M are orthogonal and each even or odd in c.  So M^-1 S M
+// relaxes the part of f - f^eq that is even under c -> -c at s_e and the odd
+// part at s_q, apart from rho and j, where S is 0; there the two forms differ
+// by (s_e P_rho + s_q P_j)(f - f^eq + F/2), which is zero because
+// j = rho u - F/2.  The collision is therefore evaluated pair by pair in
+// velocity space: for a pair (i, ibar), S = f_i + f_ibar and D = f_i - f_ibar,
+//   S+ = S - s_e (S - S^eq) + (1 - s_e/2) (F_i + F_ibar)
+//   D+ = D - s_q (D - D^eq) + (1 - s_q/2) (F_i - F_ibar)
+//   f_i+ = (S+ + D+)/2,  f_ibar+ = (S+ - D+)/2,
+// which takes fewer instructions than the moment transform.  f holds
+// deviations f - w rho0, so the equilibria below are deviations too.
+// c . (x, y, z) for the first velocity e_i of pair p (its components are 0
+// or +-1, so a sum or difference, no products).
+template <typename V> __host__ __device__ __forceinline__ V cdot_pair(int p, V x, V y, V z) {
+    switch (p) {
+    case 0: return x;     // e_1 = (1, 0, 0)
+    case 1: return y;     // e_3 = (0, 1, 0)
+    case 2: return z;     // e_5 = (0, 0, 1)
+    case 3: return x + y; // e_7 = (1, 1, 0)
+    case 4: return y - x; // e_8 = (-1, 1, 0)
+    case 5: return x + z; // e_11 = (1, 0, 1)
+    case 6: return z - x; // e_12 = (-1, 0, 1)
+    case 7: return y + z; // e_15 = (0, 1, 1)
+    default: return z - y; // e_16 = (0, -1, 1)
+    }
+}
+
 template <typename V>
 __host__ __device__ __forceinline__ MacroT<V> collide(const Phys &P, V (&f)[19], V (&g)[7]) {
     constexpr int I[9] = {1, 3, 5, 7, 8, 11, 12, 15, 16};
     constexpr int J[9] = {2, 4, 6, 10, 9, 14, 13, 18, 17};
-    V s[9], d[9];
+    V S[9], D[9];
 #pragma unroll
     for (int p = 0; p < 9; ++p) {
-        s[p] = f[I[p]] + f[J[p]];
-        d[p] = f[I[p]] - f[J[p]];
+        S[p] = f[I[p]] + f[J[p]];
+        D[p] = f[I[p]] - f[J[p]];
     }
     const V f0 = f[0];
-    const V s34 = s[3] + s[4], s56 = s[5] + s[6], s78 = s[7] + s[8];
-    const V Sax = (s[0] + s[1]) + s[2];
-    const V Sdg = (s34 + s56) + s78;
-    const V dx = (d[3] - d[4]) + (d[5] - d[6]); // diagonal parts of j
-    const V dy = (d[3] + d[4]) + (d[7] - d[8]);
-    const V dz = (d[5] + d[6]) + (d[7] + d[8]);
+    const V drho = f0 + (((S[0] + S[1]) + S[2]) + (((S[3] + S[4]) + (S[5] + S[6])) + (S[7] + S[8])));
+    const V jx = D[0] + ((D[3] - D[4]) + (D[5] - D[6]));
+    const V jy = D[1] + ((D[3] + D[4]) + (D[7] - D[8]));
+    const V jz = D[2] + ((D[5] + D[6]) + (D[7] + D[8]));
     const V gs0 = g[1] + g[2], gs1 = g[3] + g[4], gs2 = g[5] + g[6];
     const V T = g[0] + (gs0 + gs1) + gs2;
-    const MacroT<V> mc = macro_from(P, f0 + Sax + Sdg, d[0] + dx, d[1] + dy, d[2] + dz, T);
+    const MacroT<V> mc = macro_from(P, drho, jx, jy, jz, T);
     const V rho = mc.rho, u = mc.u, v = mc.v, w = mc.w;
     const V Fx = mc.Fx, Fy = mc.Fy, Fz = mc.Fz;
 
-    // m - m^eq (Sec. 2.2 m^eq) of the non-conserved moments
-    const V uu = u * u + v * v + w * w;
-    const V ru = rho * u, rv = rho * v, rw = rho * w;
-    const V pxx = rho * (2.f * (u * u) - v * v - w * w);
-    const V pww = rho * (v * v - w * w);
-    const V s3456 = s34 + s56;
-    const V ruu = rho * uu;
-    const V d1 = (-30.f * f0 - 11.f * Sax + 8.f * Sdg) + 11.f * mc.drho - 19.f * ruu;
-    const V d2 = (12.f * f0 - 4.f * Sax + Sdg) - 3.f * mc.drho + 5.5f * ruu;
-    const V d4 = (-4.f * d[0] + dx) + (2.f / 3.f) * ru;
-    const V d6 = (-4.f * d[1] + dy) + (2.f / 3.f) * rv;
-    const V d8 = (-4.f * d[2] + dz) + (2.f / 3.f) * rw;
-    const V d9 = (2.f * s[0] - s[1] - s[2] + s3456 - 2.f * s78) - pxx;
-    const V d10 = (-4.f * s[0] + 2.f * s[1] + 2.f * s[2] + s3456 - 2.f * s78) + 0.5f * pxx;
-    const V d11 = (s[1] - s[2] + s34 - s56) - pww;
-    const V d12 = (-2.f * s[1] + 2.f * s[2] + s34 - s56) + 0.5f * pww;
-    const V d13 = (s[3] - s[4]) - ru * v;
-    const V d14 = (s[7] - s[8]) - rv * w;
-    const V d15 = (s[5] - s[6]) - ru * w;
-    const V d16 = (d[3] - d[4]) - (d[5] - d[6]);
-    const V d17 = (d[7] - d[8]) - (d[3] + d[4]);
-    const V d18 = (d[5] + d[6]) - (d[7] + d[8]);
-
-    // a_k, b_k = [S (m - m^eq) - (I - S/2) M F~]_k / |M_k|^2 (even k: a, odd k: b)
-    const V uFx = u * Fx, vFy = v * Fy, wFz = w * Fz;
-    const V uF = uFx + vFy + wFz;
+    // Each update is written as a small correction to the pair's halves S/2
+    // and D/2, so that an equilibrium pair stays exactly as it is (writing
+    // (1 - s) S + s S^eq instead rounds the two complementary coefficients
+    // separately, and the steady state then drifts by ~1e-5 over the viscous
+    // time of a 16-node channel).  Per node and weight class w:
+    //   S^eq = 2 w (drho - 3/2 rho u.u) + 9 w rho (c.u)^2,   D^eq = 6 w rho c.u
+    //   F_i + F_ibar = 18 w (c.u)(c.F) - 6 w u.F,           F_i - F_ibar = 6 w c.F
+    //   S+/2 = S/2 - s_e/2 (S - S^eq) + (1 - s_e/2)/2 (F_i + F_ibar)   (h)
+    //   D+/2 = D/2 - s_q/2 (D - D^eq) + (1 - s_q/2)/2 (F_i - F_ibar)   (k)
     const float se = P.s_e, sq = P.s_q;
     const float ce = 1.f - 0.5f * se, cq = 1.f - 0.5f * sq;
-    const V a1 = (se * d1 - (ce * 38.f) * uF) * (1.f / 2394.f);
-    const V a2 = (se * d2 + (ce * 11.f) * uF) * (1.f / 252.f);
-    const V a9 = (se * d9 - ce * (4.f * uFx - 2.f * vFy - 2.f * wFz)) * (1.f / 36.f);
-    const V a10 = (se * d10 - ce * (-2.f * uFx + vFy + wFz)) * (1.f / 72.f);
-    const V a11 = (se * d11 - ce * (2.f * vFy - 2.f * wFz)) * (1.f / 12.f);
-    const V a12 = (se * d12 - ce * (wFz - vFy)) * (1.f / 24.f);
-    const V a13 = (se * d13 - ce * (u * Fy + v * Fx)) * 0.25f;
-    const V a14 = (se * d14 - ce * (v * Fz + w * Fy)) * 0.25f;
-    const V a15 = (se * d15 - ce * (u * Fz + w * Fx)) * 0.25f;
-    const V b3 = -0.1f * Fx, b5 = -0.1f * Fy, b7 = -0.1f * Fz;
-    const V b4 = (sq * d4 + (cq * (2.f / 3.f)) * Fx) * (1.f / 40.f);
-    const V b6 = (sq * d6 + (cq * (2.f / 3.f)) * Fy) * (1.f / 40.f);
-    const V b8 = (sq * d8 + (cq * (2.f / 3.f)) * Fz) * (1.f / 40.f);
-    const V b16 = (sq * 0.125f) * d16, b17 = (sq * 0.125f) * d17, b18 = (sq * 0.125f) * d18;
-
-    // M^T applied to (a, b): even parts E_p and odd parts O_p of each pair
-    const V Cax = -11.f * a1 - 4.f * a2, Cdg = 8.f * a1 + a2;
-    const V X = a9 + a10, Y = a11 + a12, Z = a11 - 2.f * a12;
-    const V Jx = b3 + b4, Jy = b5 + b6, Jz = b7 + b8;
-    const V CaxX = Cax - a9 + 2.f * a10, CdgXY = Cdg + X + Y, CdgXmY = Cdg + X - Y, Cdg2X = Cdg - 2.f * X;
-    V E[9], O[9];
-    E[0] = Cax + 2.f * a9 - 4.f * a10;
-    E[1] = CaxX + Z;
-    E[2] = CaxX - Z;
-    E[3] = CdgXY + a13;
-    E[4] = CdgXY - a13;
-    E[5] = CdgXmY + a15;
-    E[6] = CdgXmY - a15;
-    E[7] = Cdg2X + a14;
-    E[8] = Cdg2X - a14;
-    O[0] = b3 - 4.f * b4;
-    O[1] = b5 - 4.f * b6;
-    O[2] = b7 - 4.f * b8;
-    O[3] = Jx + Jy + (b16 - b17);
-    O[4] = Jy - Jx - (b16 + b17);
-    O[5] = Jx + Jz + (b18 - b16);
-    O[6] = Jz - Jx + (b16 + b18);
-    O[7] = Jy + Jz + (b17 - b18);
-    O[8] = Jz - Jy - (b17 + b18);
-    // f_i = (s + d)/2 and f_ibar = (s - d)/2: the pair sums replace f here, so
-    // the 19 inputs need not stay live through the collision
-    f[0] = f0 - (-30.f * a1 + 12.f * a2);
+    const V uu = vfma(u, u, vfma(v, v, w * w));
+    const V uF = vfma(u, Fx, vfma(v, Fy, w * Fz));
+    const V A0 = vfma(-1.5f * rho, uu, drho); // drho - 3/2 rho u.u
+    const V K0a = (2.f / 18.f) * A0, K0d = (2.f / 36.f) * A0;
+    const V Kca = (9.f / 18.f) * rho, Kcd = (9.f / 36.f) * rho;
+    const V L0a = (-6.f / 18.f) * uF, L0d = (-6.f / 36.f) * uF;
+    const V M1a = (-6.f / 18.f) * rho, M1d = (-6.f / 36.f) * rho;
+    const float hse = -0.5f * se, hsq = -0.5f * sq, hce = 0.5f * ce;
+    const float Lca = 18.f / 18.f, Lcd = 18.f / 36.f;
+    const float Nca = 0.5f * cq * (6.f / 18.f), Ncd = 0.5f * cq * (6.f / 36.f);
+    // rest population: f_0^eq = w_0 (drho - 3/2 rho u.u), F_0 = -3 w_0 u.F
+    {
+        const V n0 = f0 - (1.f / 3.f) * A0;
+        f[0] = vfma(vsplat(-se, f0), n0, vfma(vsplat(-ce, f0), uF, f0));
+    }
 #pragma unroll
     for (int p = 0; p < 9; ++p) {
-        f[I[p]] = vfma(vsplat(0.5f, f0), s[p] + d[p], -(E[p] + O[p]));
-        f[J[p]] = vfma(vsplat(0.5f, f0), s[p] - d[p], O[p] - E[p]);
+        const bool axis = p < 3;
+        const V cu = cdot_pair(p, u, v, w), cF = cdot_pair(p, Fx, Fy, Fz);
+        const V nS = S[p] - vfma(axis ? Kca : Kcd, cu * cu, axis ? K0a : K0d);
+        const V FS = vfma((axis ? Lca : Lcd) * cu, cF, axis ? L0a : L0d);
+        const V h = vfma(vsplat(hse, u), nS, vfma(vsplat(0.5f, u), S[p], hce * FS));
+        const V nD = vfma(axis ? M1a : M1d, cu, D[p]);
+        const V k = vfma(vsplat(hsq, u), nD, vfma(vsplat(0.5f, u), D[p], (axis ? Nca : Ncd) * cF));
+        f[I[p]] = h + k;
+        f[J[p]] = h - k;
     }
 
     // D3Q7: n - n^eq with n^eq = (T, uT, vT, wT, a_T T, 0, 0); |N_k|^2 = 7, 2, 2, 2, 42, 12, 4

@@ -7,7 +7,12 @@ steady state for.  Each runs at 65^3 to the steady criterion (relative
 change of the hot-wall Nu below 1e-7 over 1000 steps) from rest and from
 the network's prediction (stored weights).  Checked:
   - every run converges, and both starts of a pair land on the same Nu
-    (1e-4, the criterion's resolution);
+    within 0.1%, the steady-Nu bound of FP32 storage.  The criterion itself
+    resolves less than its 1e-7: it stops once the change per 1000 steps is
+    small, and a slow mode with an e-folding of T steps leaves ~1e-7 T/1000
+    of the way still to go; at Ra 8.3e6, Pr 6.6 the cold run's Nu was still
+    rising by 8e-6 over 300,000 steps after the criterion, and the two starts,
+    approaching from either side, stopped 1.04e-4 apart;
   - the (1e6, 0.71) runs end within 0.1% (the steady-Nu bound of FP32
     storage) of the oracle's steady Nu at 65^3
     (tests/golden/steady_side_heated_65.json);
@@ -61,7 +66,7 @@ def test_network_start_against_cold_start(ws):
             cold = ws.run_from(Ra, Pr, None, stream)
             warm = ws.run_from(Ra, Pr, pred, stream)
             assert cold["converged"] and warm["converged"], (Ra, Pr)
-            assert abs(warm["Nu"] - cold["Nu"]) <= 1e-4 * cold["Nu"], (Ra, Pr, warm["Nu"], cold["Nu"])
+            assert abs(warm["Nu"] - cold["Nu"]) <= 1e-3 * cold["Nu"], (Ra, Pr, warm["Nu"], cold["Nu"])
             speedups.append(cold["steps"] / warm["steps"])
         assert abs(warm["Nu"] - oracle_nu) <= 1e-3 * oracle_nu, (warm["Nu"], oracle_nu)
         assert abs(cold["Nu"] - oracle_nu) <= 1e-3 * oracle_nu, (cold["Nu"], oracle_nu)
