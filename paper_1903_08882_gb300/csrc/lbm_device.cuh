@@ -471,7 +471,12 @@ template <typename V> __host__ __device__ __forceinline__ V cdot_pair(int p, V x
     }
 }
 
-template <typename V>
+// GSC: g holds the thermal populations times kGScale (the FP16 storage's
+// stored values, not scaled back).  The D3Q7 update is linear and
+// homogeneous in (g, T), and a power-of-two scale commutes with FP32
+// rounding, so it runs on the scaled values unchanged and bit for bit the
+// same; only T for the force and the returned moments is scaled back.
+template <typename V, bool GSC = false>
 __host__ __device__ __forceinline__ MacroT<V> collide(const Phys &P, V (&f)[19], V (&g)[7]) {
     constexpr int I[9] = {1, 3, 5, 7, 8, 11, 12, 15, 16};
     constexpr int J[9] = {2, 4, 6, 10, 9, 14, 13, 18, 17};
@@ -488,7 +493,7 @@ __host__ __device__ __forceinline__ MacroT<V> collide(const Phys &P, V (&f)[19],
     const V jz = D[2] + ((D[5] + D[6]) + (D[7] + D[8]));
     const V gs0 = g[1] + g[2], gs1 = g[3] + g[4], gs2 = g[5] + g[6];
     const V T = g[0] + (gs0 + gs1) + gs2;
-    const MacroT<V> mc = macro_from(P, drho, jx, jy, jz, T);
+    const MacroT<V> mc = macro_from(P, drho, jx, jy, jz, GSC ? kGUnscale * T : T);
     const V rho = mc.rho, u = mc.u, v = mc.v, w = mc.w;
     const V Fx = mc.Fx, Fy = mc.Fy, Fz = mc.Fz;
 
