@@ -26,7 +26,7 @@
 // kXfMinNx nodes the nodes at x = 0 and x = nx-1 of those rows are updated
 // here too: the six values that arrive through the x face (bounce-back from
 // the node's own slot, or the far end of the row when x is periodic) are not
-// in the shifted windows, so the issuing warp fetches each as one 4-byte
+// in the shifted windows, so a second warp fetches each as one 4-byte
 // asynchronous copy (cp.async) into the stage, completing on the stage's
 // barrier, and the links that leave through the face are stored to the
 // node's own slots.  The nodes next to a y or z face (and, for shorter rows,
@@ -147,7 +147,11 @@ template <int FMT> struct PairF {
     static __device__ __forceinline__ void st1s(E *p, float v, uint32_t r) { Store<FMT>::sts(p, v, r); }
 };
 template <int S> using PF = PairF<FS(S)>; // flow arrays
-template <int S> using PG = PairF<GS(S)>; // thermal arrays
+// thermal arrays: the FP16 thermal format's stored (2^12-scaled) values are
+// used as they are, and the collision runs on them (collide<V, true>)
+template <int S> constexpr bool kGRaw = GS(S) == ST_F16T;
+template <int S> using PG = PairF<kGRaw<S> ? ST_F16 : GS(S)>;
+template <int S> constexpr float kGs = kGRaw<S> ? kGScale : 1.f; // scale of g as held in registers
 
 // Flat offset of e_i for population q (0..18 flow, 19..25 thermal: the D3Q7
 // velocities e_0..e_6 equal the D3Q19 ones).
@@ -196,8 +200,8 @@ template <bool ODD> __device__ __forceinline__ TileSpan tile_span(const Geom &G,
 // holding it into the stage's x-face area, word (2 R + side) 6 + j for the
 // face node of the tile's R-th row on side 0 (x = 0) or 1 (x = nx-1) and
 // its link j (five flow links, then the thermal one), completion counted on
-// the same barrier.
-template <int S, bool ODD, bool XF>
+// the same barrier (issue_side, run by another warp).
+template <int S, bool ODD>
 __device__ __forceinline__ void issue_tile(const SF<S> *f, const SG<S> *g, const Geom &G, const TileSpan &sp,
                                            unsigned char *stage, int *wofs, uint64_t *bar, int lane) {
     unsigned sz = 0;
@@ -223,29 +227,35 @@ __device__ __forceinline__ void issue_tile(const SF<S> *f, const SG<S> *g, const
     if (lane == 0) mbar_expect_tx(bar, total);
     __syncwarp();
     if (sz) bulk_load(stage + Stage<S>::offset(lane), src, sz, bar);
-    if (XF) {
-        uint32_t *side = reinterpret_cast<uint32_t *>(stage + Stage<S>::win);
-        const uint32_t nx = (uint32_t)G.nx;
-        const uint32_t row0 = fast_div(sp.n0, G.mag_nx);
-        const uint32_t rows = fast_div(sp.n0 + (uint32_t)kTile - 1u, G.mag_nx) - row0 + 1u;
-        const uint32_t beg = sp.n0 > sp.lo ? sp.n0 : sp.lo;
-        const uint32_t end = sp.n0 + (uint32_t)kTile < sp.hi ? sp.n0 + (uint32_t)kTile : sp.hi;
-        const bool per = G.periodic & 1;
-        const int64_t s = G.stride;
-        for (uint32_t k = (uint32_t)lane; k < rows * 12u; k += 32u) {
-            const uint32_t R = k / 12u, rem = k - 12u * R, sd = rem / 6u, j = rem - 6u * sd;
-            const uint32_t n = (row0 + R) * nx + (sd ? nx - 1u : 0u);
-            if (n < beg || n >= end) continue;
-            const int q = j < 5u ? xlink((int)sd, (int)j) : 1 + (int)sd; // flow / thermal link index
-            // wall: the node's own slot q; periodic: slot qbar of n - e_q wrapped along the row
-            const int64_t at = per ? (int64_t)n - G.off[q] + (sd ? -(int64_t)nx : (int64_t)nx) : (int64_t)n;
-            const int arr = per ? opp_idx(q) : q;
-            const char *p = j < 5u ? reinterpret_cast<const char *>(f + (int64_t)arr * s + at)
-                                   : reinterpret_cast<const char *>(g + (int64_t)arr * s + at);
-            word_load(side + k, reinterpret_cast<const void *>(reinterpret_cast<uintptr_t>(p) & ~(uintptr_t)3));
-        }
-        word_arrive(bar);
+}
+
+// The x-face words of a tile (see issue_tile), fetched by all 32 lanes of a
+// second warp so that the issuing work is split between two warps: each
+// lane's copies complete on the stage's barrier through one counted arrival.
+template <int S>
+__device__ __forceinline__ void issue_side(const SF<S> *f, const SG<S> *g, const Geom &G, const TileSpan &sp,
+                                           unsigned char *stage, uint64_t *bar, int lane) {
+    uint32_t *side = reinterpret_cast<uint32_t *>(stage + Stage<S>::win);
+    const uint32_t nx = (uint32_t)G.nx;
+    const uint32_t row0 = fast_div(sp.n0, G.mag_nx);
+    const uint32_t rows = fast_div(sp.n0 + (uint32_t)kTile - 1u, G.mag_nx) - row0 + 1u;
+    const uint32_t beg = sp.n0 > sp.lo ? sp.n0 : sp.lo;
+    const uint32_t end = sp.n0 + (uint32_t)kTile < sp.hi ? sp.n0 + (uint32_t)kTile : sp.hi;
+    const bool per = G.periodic & 1;
+    const int64_t s = G.stride;
+    for (uint32_t k = (uint32_t)lane; k < rows * 12u; k += 32u) {
+        const uint32_t R = k / 12u, rem = k - 12u * R, sd = rem / 6u, j = rem - 6u * sd;
+        const uint32_t n = (row0 + R) * nx + (sd ? nx - 1u : 0u);
+        if (n < beg || n >= end) continue;
+        const int q = j < 5u ? xlink((int)sd, (int)j) : 1 + (int)sd; // flow / thermal link index
+        // wall: the node's own slot q; periodic: slot qbar of n - e_q wrapped along the row
+        const int64_t at = per ? (int64_t)n - G.off[q] + (sd ? -(int64_t)nx : (int64_t)nx) : (int64_t)n;
+        const int arr = per ? opp_idx(q) : q;
+        const char *p = j < 5u ? reinterpret_cast<const char *>(f + (int64_t)arr * s + at)
+                               : reinterpret_cast<const char *>(g + (int64_t)arr * s + at);
+        word_load(side + k, reinterpret_cast<const void *>(reinterpret_cast<uintptr_t>(p) & ~(uintptr_t)3));
     }
+    word_arrive(bar);
 }
 
 // x-face node (hi = false: x = 0, true: x = nx-1) of component K of a pair:
@@ -274,7 +284,7 @@ __device__ __forceinline__ void xface_in(float2 (&fl)[19], float2 (&gl)[7], cons
     const int oq = hi ? G.off[2] : G.off[1];
     const uint32_t at = per ? (uint32_t)((int64_t)n - oq + wrap) : n;
     float v = PG<S>::word(w[5], at & 1u);
-    if (!per && ((P.dir_mask >> (hi ? 1 : 0)) & 1)) v = (hi ? P.abbT[1] : P.abbT[0]) - v; // through the face
+    if (!per && ((P.dir_mask >> (hi ? 1 : 0)) & 1)) v = kGs<S> * (hi ? P.abbT[1] : P.abbT[0]) - v; // through the face
     if (hi) set_k<K>(gl[2], v);
     else set_k<K>(gl[1], v);
 }
@@ -305,7 +315,7 @@ __device__ __forceinline__ void xface_out(SF<S> *f, SG<S> *g, const float2 (&fl)
         p = g + q * s + ((int64_t)n + (hi ? G.off[1] : G.off[2]) - wrap);
     } else {
         p = g + (hi ? 2 : 1) * s + n; // the opposite slot
-        if ((P.dir_mask >> (hi ? 1 : 0)) & 1) v = (hi ? P.abbT[1] : P.abbT[0]) - v; // leaves through the face
+        if ((P.dir_mask >> (hi ? 1 : 0)) & 1) v = kGs<S> * (hi ? P.abbT[1] : P.abbT[0]) - v; // leaves through the face
     }
     PG<S>::st1s(p, v, rnd_pop(rb, q));
 }
@@ -329,11 +339,14 @@ __global__ void __launch_bounds__(kThreads, 2)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();
-    if (warp == 0) {
+    if (warp == 0 || (XF && warp == 1)) {
         for (int k = 0; k < NST; ++k) {
             const uint32_t t = blockIdx.x + (uint32_t)k * gridDim.x;
-            if (t < ntiles)
-                issue_tile<S, ODD, XF>(f, g, G, tile_span<ODD>(G, T, t), stages + k * Stage<S>::bytes,
+            if (t >= ntiles) continue;
+            if (warp == 1)
+                issue_side<S>(f, g, G, tile_span<ODD>(G, T, t), stages + k * Stage<S>::bytes, &bar[k], lane);
+            else
+                issue_tile<S, ODD>(f, g, G, tile_span<ODD>(G, T, t), stages + k * Stage<S>::bytes,
                                        wofs + kWofs * k, &bar[k], lane);
         }
     }
@@ -415,7 +428,7 @@ __global__ void __launch_bounds__(kThreads, 2)
                     if (lo1 || hi1) xface_in<S, 1>(fl, gl, side + 12u * (r1 - row0) + (hi1 ? 6u : 0u), mb, hi1, G, P);
                 }
             }
-            collide(P, fl, gl);
+            collide<float2, kGRaw<S>>(P, fl, gl);
             SF<S> *fo = f;
             SG<S> *go = g;
             asm volatile("" : "+l"(fo), "+l"(go)); // recompute addresses after the collision
@@ -472,10 +485,12 @@ __global__ void __launch_bounds__(kThreads, 2)
             }
             return;
         }
-        if (warp == 0) {
+        if (warp == 0 || (XF && warp == 1)) {
             const uint32_t tn = t + (uint32_t)NST * gridDim.x;
-            if (tn < ntiles)
-                issue_tile<S, ODD, XF>(f, g, G, tile_span<ODD>(G, T, tn), stages + st * Stage<S>::bytes,
+            if (tn < ntiles && warp == 1)
+                issue_side<S>(f, g, G, tile_span<ODD>(G, T, tn), stages + st * Stage<S>::bytes, &bar[st], lane);
+            else if (tn < ntiles)
+                issue_tile<S, ODD>(f, g, G, tile_span<ODD>(G, T, tn), stages + st * Stage<S>::bytes,
                                        wofs + kWofs * st, &bar[st], lane);
         }
     }
