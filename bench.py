@@ -436,6 +436,62 @@ def bench_batched(lbm, args, stream):
     return res
 
 
+def bench_warmstart_network(stream, edge=129, reps=5):
+    """Forward and backward of the warm-start U-Net (one sample, 129^3 fine
+    lattice, random weights and inputs), on its own kernels: the whole
+    network's times and the convolutions' algorithmic FLOP rate (2 x voxels
+    x Cin x Cout x 27 per convolution; the backward pass does the data and
+    the weight gradient, twice that), against the measured BF16 dense rate
+    of the tensor cores (the convolutions multiply BF16 weights with FP32
+    operands carried as two BF16 terms, so their MMAs do 2-3x these FLOPs)."""
+    import torch
+
+    from paper_1903_08882_gb300 import unet
+
+    size = (edge, edge, edge)
+    net = unet.UNet(size, seed=1)
+    g = torch.Generator(device="cuda").manual_seed(2)
+    x = torch.rand((7,) + size, device="cuda", generator=g) - 0.5
+    t = torch.rand((5,) + size, device="cuda", generator=g) - 0.5
+    flops = 0.0
+    for name, cin, cout in unet.layer_shapes():
+        lvl = 0 if name == "head" else int(name[1])
+        v = net.sizes[lvl][0] * net.sizes[lvl][1] * net.sizes[lvl][2]
+        flops += 2.0 * v * cin * cout * 27
+    with torch.cuda.stream(stream):
+        for _ in range(2):
+            net.zero_grad()
+            net.forward(x)
+            net.backward(x, t)
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        fw = bw = 0.0
+        for _ in range(reps):
+            net.zero_grad()
+            e0.record(stream)
+            net.forward(x)
+            e1.record(stream)
+            net.backward(x, t)
+            e2.record(stream)
+            e2.synchronize()
+            fw += e0.elapsed_time(e1)
+            bw += e1.elapsed_time(e2)
+    fw, bw = fw / reps, bw / reps
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peak, kind = float(json.load(fh)["bf16_tflops"]), "measured"
+    except Exception:
+        peak, kind = 1900.0, "fallback"
+    ach_f, ach_b = flops / (fw * 1e-3) / 1e12, 2 * flops / (bw * 1e-3) / 1e12
+    del net
+    return {"size": list(size), "forward_ms": round(fw, 3), "backward_ms": round(bw, 3),
+            "conv_gflop_forward": round(flops / 1e9, 2),
+            "roofline": {"bound": "tensor", "unit": "TFLOP/s", "peak": peak, "peak_kind": kind,
+                         "achieved_forward": round(ach_f, 2), "achieved_backward": round(ach_b, 2),
+                         "frac_forward": round(ach_f / peak, 4), "frac_backward": round(ach_b / peak, 4)},
+            "kernels": "k_conv_fwd_tc (forward and data gradient), k_conv_bww_tc (weight gradient): mma.sync "
+                       "m16n8k16 BF16 -> FP32"}
+
+
 def run_gpu(args):
     import torch
 
@@ -447,6 +503,10 @@ def run_gpu(args):
         _build.build()
     stream = torch.cuda.Stream()
     peak, peak_kind = _peak_hbm()
+    if args.unet_only:  # profiling run of the warm-start network alone
+        if rank == 0:
+            print(json.dumps({"warmstart_network": bench_warmstart_network(stream)}), flush=True)
+        return
     storages = ["fp32"] if args.fp32_only else ["fp32", "fp16s", "bf16s", "fp16m"]
     if args.only:
         storages = [args.only]
@@ -481,6 +541,7 @@ def run_gpu(args):
     if not args.no_batch and ws == 1:
         with torch.cuda.stream(stream):
             batched = bench_batched(lbm, args, stream)
+    network = bench_warmstart_network(stream) if ws == 1 and not args.no_batch else None
     cpu_rate, threads, sample = _cpu_oracle_rate() if not args.no_cpu else (None, None, None)
     line = {
         "metric": METRIC, "value": round(main["glups"], 3), "unit": "GLUPS", "n_gpus": ws,
@@ -508,6 +569,7 @@ def run_gpu(args):
         "diagnostics": main.get("diagnostics"),
         "Nu_hot_after_run": main["Nu_hot"],
         "batched_sweep": batched,
+        "warmstart_network": network,
     }
     print(json.dumps(line), flush=True)
 
@@ -526,6 +588,7 @@ def main():
     ap.add_argument("--only", default=None, choices=["fp32", "fp16s", "bf16s", "fp16m"],
                     help="time one storage form only (profiling)")
     ap.add_argument("--npt", type=int, default=0, help="nodes per thread of the AA kernels (0: library default)")
+    ap.add_argument("--unet-only", action="store_true", help="time the warm-start network alone (profiling)")
     args = ap.parse_args()
     N_EDGE = args.edge
     if args.impl == "reference":
