@@ -434,10 +434,10 @@ lbm_status lbm_create(const lbm_params *params, const lbm_allocator *alloc, void
         int per_sm = 0, nsm = 0;
         if (staged_prepare(params->storage, &per_sm) == cudaSuccess && per_sm > 0 &&
             cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->dev) == cudaSuccess && nsm > 0) {
-            const uint32_t tile = (uint32_t)staged_tile_nodes();
+            const uint32_t tile_even = (uint32_t)staged_tile_nodes(0), tile_odd = (uint32_t)staged_tile_nodes(1);
             StagedGeom &T = ctx->T;
-            T.even_tiles = (uint32_t)((c.nodes + tile - 1) / tile);
-            T.tpp = (G.nxy - 2u * (uint32_t)G.nx + 1u + tile - 1u) / tile;
+            T.even_tiles = (uint32_t)((c.nodes + tile_even - 1) / tile_even);
+            T.tpp = (G.nxy - 2u * (uint32_t)G.nx + 1u + tile_odd - 1u) / tile_odd;
             T.mag_tpp = magic_of(T.tpp);
             T.odd_tiles = T.tpp * (uint32_t)(G.nz - 2);
             T.grid = nsm * per_sm; // persistent: every block resident

@@ -55,8 +55,8 @@ cudaError_t launch_staged(const StepArgs &a);
 // Opt in to the staged kernels' shared memory and report how many blocks of
 // them fit on an SM.
 cudaError_t staged_prepare(int storage, int *blocks_per_sm);
-int staged_smem_bytes(int storage);
-int staged_tile_nodes();
+// nodes per tile of the even (odd = 0) and odd (odd = 1) staged step
+int staged_tile_nodes(int odd);
 int staged_xf_min_nx();
 // Fills T.soff for the storage format and lattice.
 void staged_store_offsets(int storage, const Geom &G, StagedGeom &T);

@@ -96,12 +96,12 @@ SCHEMES = {  # streaming, nodes per thread, AA pipeline
                                (101, 9, 5), (16, 40, 6), (17, 45, 5)])
 def test_random_state_steps(lbm, walls, scheme, n):
     """AA register kernels with one and two nodes per thread, the staged AA
-    kernels, and the pull scheme.  45 x 37 x 13 spans several 512-node tiles
+    kernels, and the pull scheme.  45 x 37 x 13 spans several 448-node tiles
     per plane of the staged kernels with a ragged tail; 80 x 7 x 6 and
     101 x 9 x 5 give the two-node-per-thread row kernel, which updates the
     x-face nodes of its rows itself, runs of several warps per row; 16 x 40
     x 6 and 17 x 45 x 5 put dozens of rows (and x-face nodes) into one
-    512-node tile of the staged kernels."""
+    448-node tile of the staged kernels."""
     p = _orc_params(n, WALLS[walls])
     f0, g0 = _random_state(p, 3)
     streaming, npt, pipe = SCHEMES[scheme]
