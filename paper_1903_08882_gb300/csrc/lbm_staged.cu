@@ -539,7 +539,6 @@ __global__ void __launch_bounds__(kThreads, 2)
             // this warp is done with the stage
             __syncwarp();
             if (lane == 0) mbar_arrive(&empty[st]);
-            if (v0 || v1) update_pair<S, ODD, XF>(f, g, G, P, T, fl, gl, m, mb, v0, v1, lo0, hi0, lo1, hi1);
             if (!ODD && warp == 0) { // refill the stage once every warp has read it
                 const uint32_t tn = t + (uint32_t)NST * gridDim.x;
                 if (tn < ntiles) {
@@ -553,6 +552,7 @@ __global__ void __launch_bounds__(kThreads, 2)
                     if (lane == 0) fills[st] = j / NST + 2;
                 }
             }
+            if (v0 || v1) update_pair<S, ODD, XF>(f, g, G, P, T, fl, gl, m, mb, v0, v1, lo0, hi0, lo1, hi1);
         }
     }
     // after a timeout, let the copies still in flight land before the block exits
