@@ -40,8 +40,12 @@ BYTES_PER_NODE = {"fp32": 208, "fp16s": 104, "bf16s": 104, "fp16m": 132}  # 26 p
 NOMINAL_HBM_GBS = 8000.0
 FALLBACK_HBM_GBS = 6800.0
 METRIC = "GLUPS (D3Q19+D3Q7) and % HBM roofline at 257^3, FP32 vs FP16 storage"
-STEP_KERNEL_SRC = [os.path.join(ROOT, "paper_1903_08882_gb300", "csrc", f)
-                   for f in ("lbm_kernels.cu", "lbm_staged.cu", "lbm_device.cuh")]
+# sources of each storage's step kernels: FP32 runs the register kernels, the
+# 2-byte storages the staged kernels (plus the register face kernel)
+STEP_KERNEL_SRC = {
+    "fp32": ("lbm_kernels.cu", "lbm_device.cuh"),
+    "staged": ("lbm_kernels.cu", "lbm_staged.cu", "lbm_device.cuh"),
+}
 # kernels of one LB time step with the library's default kernels per storage
 STEP_KERNELS = {
     "fp32": "k_aa_even2 (even steps); k_aa_odd_rows + k_aa_odd_face on the y/z-face nodes (odd steps)",
@@ -58,12 +62,13 @@ def _peak_hbm():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def _kernel_hash():
-    """Hash of the step kernels' code: sources with comments and whitespace
-    removed, so that only a change of the code invalidates stored counters."""
+def _kernel_hash(storage):
+    """Hash of a storage's step kernels' code: sources with comments and
+    whitespace removed, so that only a change of the code invalidates stored
+    counters."""
     h = hashlib.sha256()
-    for p in STEP_KERNEL_SRC:
-        with open(p) as fh:
+    for f in STEP_KERNEL_SRC["fp32" if storage == "fp32" else "staged"]:
+        with open(os.path.join(ROOT, "paper_1903_08882_gb300", "csrc", f)) as fh:
             src = fh.read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
         src = re.sub(r"//[^\n]*", "", src)
@@ -78,8 +83,8 @@ def _profiled_traffic(storage):
     if not os.path.exists(path):
         return None
     txt = open(path).read()
-    m = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
-    if not m or m.group(1) != _kernel_hash():
+    m = re.search(rf"kernel_source_sha256_16_{storage}:\s*([0-9a-f]+)", txt)
+    if not m or m.group(1) != _kernel_hash(storage):
         return None
     m = re.search(rf"traffic_per_launch_{storage}_257:\s*([0-9.eE+]+)", txt)
     return float(m.group(1)) if m else None
