@@ -51,24 +51,6 @@ __device__ __forceinline__ double warp_max(double v) {
     return v;
 }
 
-// Sum (max for slot 16) of v[k] over the block; result valid in thread 0.
-__device__ __forceinline__ void block_reduce(double (&v)[kNDiag], double (*sh)[kNDiag]) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-    for (int k = 0; k < kNDiag; ++k) {
-        const double r = k == 16 ? warp_max(v[k]) : warp_sum(v[k]);
-        if (lane == 0) sh[wid][k] = r;
-    }
-    __syncthreads();
-    if (wid == 0) {
-#pragma unroll
-        for (int k = 0; k < kNDiag; ++k) {
-            double r = lane < nw ? sh[lane][k] : 0.0;
-            v[k] = k == 16 ? warp_max(r) : warp_sum(r);
-        }
-    }
-}
-
 // Double-float value hi + lo (two FP32 words, about 48 significant bits).
 // FP64 arithmetic is slow on this GPU, so the warp stage of the reductions
 // adds these pairs with FP32 instructions (Knuth's error-free TwoSum, then a
@@ -127,44 +109,28 @@ __device__ __forceinline__ float dval(float pm, float p0, float pp, bool wm, boo
 // Diagnostic sums of one sample.  The lattice is cut into columns of
 // kDiagTX x kDiagTY nodes in x, y and segments of kDiagSeg planes in z; a
 // block takes one such brick at a time (bricks strided over the grid, so any
-// grid size works) and marches up its planes.  The planes of the brick (u,
-// v, w, T with a one-node halo in x and y for the derivatives, and
-// rho - rho0) stream through a ring of kDiagRing plane buffers in shared
-// memory: every thread copies its own column's values and its share of the
-// halo with 4-byte asynchronous copies (cp.async), kDiagAhead planes ahead
-// of the plane being reduced, so that the memory latency is covered by the
-// work on the planes in between, and one block barrier per plane publishes
-// a plane once all its copies have landed.  Every field value is read from
-// memory about once (the halo and the two planes that start a segment add
-// ~15%).  A warp whose nodes have no wall or wrap next to them takes plain
-// central differences.  Each thread sums its column of a brick (at most
-// kDiagSeg nodes) in FP32 and adds the column sums into FP32 totals (a few
-// dozen at most); the wall terms of a column (x and y faces) or of a
-// plane (z faces) go into shared FP64 sums.
+// grid size works) and each thread marches up its column.  A thread keeps
+// its column's u, v, w, T of the planes z - 1, z and z + 1 in registers
+// (the z derivatives) and loads plane z + 2 one plane ahead; the x and y
+// neighbours come straight from memory, where the block's other lanes and
+// warps have just read them (L1 hits), so every field value leaves HBM about
+// once without shared-memory staging or a block barrier per plane.  A warp
+// whose nodes have no wall or wrap next to them takes plain central
+// differences.  Each thread sums its column of a brick (at most kDiagSeg
+// nodes) in FP32 and adds the column sums into FP32 totals (a few dozen at
+// most); the wall terms of a column (x and y faces) or of a plane (z faces)
+// go into shared FP64 sums.
 constexpr int kDiagTX = 32, kDiagTY = kDiagThreads / kDiagTX, kDiagSeg = 32;
-constexpr int kDiagAhead = 3;              // planes in flight beyond the three being read
-constexpr int kDiagRing = kDiagAhead + 4;  // the slot written at plane z was last read at plane z - 2
-struct DiagPlane {
-    float f[4][kDiagTY + 2][kDiagTX + 2]; // u, v, w, T with halo
-    float d[kDiagTY][kDiagTX];            // rho - rho0
-};
-
-__device__ __forceinline__ void cp4(void *dst, const void *src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
-                 "l"(src)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N> __device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 __global__ void __launch_bounds__(kDiagThreads, 3) k_diag(const float *__restrict__ mom, Geom G, Phys P,
                                                        WallT W, double *__restrict__ partial) {
     __shared__ double sh[kDiagThreads / 32][kNDiag];
-    __shared__ DiagPlane ring[kDiagRing];
     __shared__ double wall[12]; // slots 8..13 and 18..23
+    __shared__ float tot[9][kDiagThreads]; // slots 1..7, 14, 15: sums of each thread's column sums
     const int tx = threadIdx.x % kDiagTX, ty = threadIdx.x / kDiagTX;
     if (threadIdx.x < 12) wall[threadIdx.x] = 0.0;
-    float tot[9] = {}; // slots 1..7, 14, 15: sums of the thread's column sums
+#pragma unroll
+    for (int k = 0; k < 9; ++k) tot[k][threadIdx.x] = 0.f;
     float umax2 = 0.f;
     uint32_t count = 0, bad = 0;
     const int64_t s = G.stride;
@@ -183,109 +149,96 @@ __global__ void __launch_bounds__(kDiagThreads, 3) k_diag(const float *__restric
         const int x = ib * kDiagTX + tx, y = jb * kDiagTY + ty;
         const bool col = x < nx && y < ny;
         const int z0 = kb * kDiagSeg, z1 = min(nz, z0 + kDiagSeg);
-        const uint32_t c = (uint32_t)(col ? x : 0) + (uint32_t)nx * (uint32_t)(col ? y : 0); // column offset
-        // halo cells this thread copies: row y - 1 or y + kDiagTY (hy), column
-        // x - 1 or x + kDiagTX (hx), as flat in-plane offsets, -1 where none
-        int64_t hy = -1, hx = -1;
-        if (ty == 0 || ty == kDiagTY - 1) {
-            const int yh = ty == 0 ? jb * kDiagTY - 1 : jb * kDiagTY + kDiagTY;
-            const int yw = yh < 0 ? (pery ? ny - 1 : -1) : yh >= ny ? (pery ? yh - ny : -1) : yh;
-            if (yw >= 0 && x < nx) hy = (int64_t)x + (int64_t)nx * yw;
-        }
-        if (tx == 0 || tx == kDiagTX - 1) {
-            const int xh = tx == 0 ? ib * kDiagTX - 1 : ib * kDiagTX + kDiagTX;
-            const int xw = xh < 0 ? (perx ? nx - 1 : -1) : xh >= nx ? (perx ? xh - nx : -1) : xh;
-            if (xw >= 0 && y < ny) hx = (int64_t)xw + (int64_t)nx * y;
-        }
-        const int ry = ty == 0 ? 0 : kDiagTY + 1, cx = tx == 0 ? 0 : kDiagTX + 1;
+        const int64_t c = col ? (int64_t)x + (int64_t)nx * y : 0; // column offset
+        const bool xlo = x == 0 && !perx, xhi = x == nx - 1 && !perx;
+        const bool ylo = y == 0 && !pery, yhi = y == ny - 1 && !pery;
+        // in-plane offsets of the x and y neighbours (wrapped on periodic
+        // axes; 0, the node itself, behind a wall, where no value is used)
+        const int oxm = x > 0 ? -1 : perx ? nx - 1 : 0, oxp = x < nx - 1 ? 1 : perx ? -(nx - 1) : 0;
+        const int oym = y > 0 ? -nx : pery ? nx * (ny - 1) : 0, oyp = y < ny - 1 ? nx : pery ? -nx * (ny - 1) : 0;
+        const bool wrapxy = (perx && (x == 0 || x == nx - 1)) || (pery && (y == 0 || y == ny - 1));
         // the Dirichlet x and y faces this column lies on (-1: none; nx, ny >= 3,
         // so at most one of each) and its wall terms summed over the brick
         const int fxc = !col || perx ? -1 : (x == 0 && dir[0]) ? 0 : (x == nx - 1 && dir[1]) ? 1 : -1;
         const int fyc = !col || pery ? -1 : (y == 0 && dir[2]) ? 2 : (y == ny - 1 && dir[3]) ? 3 : -1;
         float wxa = 0.f, wxb = 0.f, wya = 0.f, wyb = 0.f;
-        // plane zz (z0 - 1 <= zz <= z1) of the brick into its ring slot; planes
-        // outside the lattice (no periodic wrap) are not copied and never read
-        auto issue = [&](int zz) {
+        // u, v, w, T (and rho - rho0) of the column in plane zz, wrapped on a
+        // periodic z; planes outside the lattice are never read
+        auto plane_of = [&](int zz) -> int64_t {
             const int za = zz < 0 ? (perz ? zz + nz : -1) : zz >= nz ? (perz ? zz - nz : -1) : zz;
-            if (zz <= z1 && za >= 0) {
-                DiagPlane &r = ring[(zz - z0 + 1) % kDiagRing];
-                const int64_t pz = (int64_t)G.nxy * za;
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    if (col) cp4(&r.f[q][ty + 1][tx + 1], F[q] + pz + c);
-                    if (hy >= 0) cp4(&r.f[q][ry][tx + 1], F[q] + pz + hy);
-                    if (hx >= 0) cp4(&r.f[q][ty + 1][cx], F[q] + pz + hx);
-                }
-                if (col) cp4(&r.d[ty][tx], dr + pz + c);
-            }
-            cp_commit(); // one group per plane, empty or not, so that the counts line up
+            return za < 0 ? -1 : (int64_t)G.nxy * za;
         };
-        for (int zz = z0 - 1; zz <= z0 + kDiagAhead; ++zz) issue(zz);
+        float pm[4] = {}, p0[4] = {}, pp[4] = {}, nn[4] = {};
+        float d0 = 0.f, dn = 0.f;
+        if (col) {
+            const int64_t am = plane_of(z0 - 1), a0 = plane_of(z0), ap = plane_of(z0 + 1);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (am >= 0) pm[q] = F[q][am + c];
+                p0[q] = F[q][a0 + c];
+                if (ap >= 0) pp[q] = F[q][ap + c];
+            }
+            d0 = dr[a0 + c];
+        }
         float bs[9]; // plain FP32 sums over the brick's column (at most kDiagSeg nodes)
 #pragma unroll
         for (int k = 0; k < 9; ++k) bs[k] = 0.f;
         for (int z = z0; z < z1; ++z) {
-            issue(z + 1 + kDiagAhead);
-            cp_wait<kDiagAhead>(); // this thread's copies of the planes up to z + 1
-            __syncthreads();       // ... and everyone's
-            const DiagPlane &Rm = ring[(z - z0) % kDiagRing], &R0 = ring[(z - z0 + 1) % kDiagRing],
-                            &Rp = ring[(z - z0 + 2) % kDiagRing];
-            const bool zlo = z == 0 && !perz, zhi = z == nz - 1 && !perz;
-            const uint32_t plane = G.nxy * (uint32_t)z;
-            float p0[4], pm[4], pp[4];
+            const int64_t pz = (int64_t)G.nxy * z;
+            // plane z + 2 for the next plane's z + 1
+            if (col && z + 1 < z1) {
+                const int64_t an = plane_of(z + 2);
+                if (an >= 0) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                p0[q] = R0.f[q][ty + 1][tx + 1];
-                pm[q] = Rm.f[q][ty + 1][tx + 1];
-                pp[q] = Rp.f[q][ty + 1][tx + 1];
+                    for (int q = 0; q < 4; ++q) nn[q] = F[q][an + c];
+                }
+                dn = dr[pz + G.nxy + c]; // z + 1 < z1 <= nz
             }
-            const bool xlo = x == 0 && !perx, xhi = x == nx - 1 && !perx;
-            const bool ylo = y == 0 && !pery, yhi = y == ny - 1 && !pery;
-            // the last node of a periodic axis that ends inside the tile reads
-            // its wrapped neighbour (node 0 of the axis) from memory
-            const bool wrapx = perx && x == nx - 1 && tx < kDiagTX - 1;
-            const bool wrapy = pery && y == ny - 1 && ty < kDiagTY - 1;
+            const bool zlo = z == 0 && !perz, zhi = z == nz - 1 && !perz;
             // a warp with no wall and no wrap among its nodes takes central
             // differences throughout
-            const bool plain = !col || !(xlo || xhi || ylo || yhi || zlo || zhi || wrapx || wrapy);
+            const bool plain = !col || !(xlo || xhi || ylo || yhi || zlo || zhi || wrapxy);
             const bool fast = __all_sync(0xffffffffu, plain);
             if (col) {
+                const int64_t n = pz + c;
                 float du[3][3], gT[3];
+                float tx1 = 0.f, ty1 = 0.f; // T of the next node inward from an x / y face
+                // x then y: the neighbours of one axis at a time, so that only
+                // eight of them are live
+#pragma unroll
+                for (int a = 0; a < 2; ++a) {
+                    const int om = a == 0 ? oxm : oym, op = a == 0 ? oxp : oyp;
+                    const bool wlo = a == 0 ? xlo : ylo, whi = a == 0 ? xhi : yhi;
+                    float vm[4], vp[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        vm[q] = F[q][n + om];
+                        vp[q] = F[q][n + op];
+                    }
+                    if (fast) {
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) du[a][q] = 0.5f * (vp[q] - vm[q]);
+                        gT[a] = 0.5f * (vp[3] - vm[3]);
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) du[a][q] = dval(vm[q], p0[q], vp[q], wlo, whi, true, 0.f, true, 0.f);
+                        gT[a] = dval(vm[3], p0[3], vp[3], wlo, whi, dir[2 * a], W.Tw[2 * a], dir[2 * a + 1],
+                                     W.Tw[2 * a + 1]);
+                    }
+                    const float t1 = (a == 0 ? fxc == 0 : fyc == 2) ? vp[3] : vm[3];
+                    if (a == 0) tx1 = t1;
+                    else ty1 = t1;
+                }
                 if (fast) {
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const float gx = 0.5f * (R0.f[q][ty + 1][tx + 2] - R0.f[q][ty + 1][tx]);
-                        const float gy = 0.5f * (R0.f[q][ty + 2][tx + 1] - R0.f[q][ty][tx + 1]);
-                        const float gz = 0.5f * (pp[q] - pm[q]);
-                        if (q < 3) {
-                            du[0][q] = gx;
-                            du[1][q] = gy;
-                            du[2][q] = gz;
-                        } else {
-                            gT[0] = gx;
-                            gT[1] = gy;
-                            gT[2] = gz;
-                        }
-                    }
+                    for (int q = 0; q < 3; ++q) du[2][q] = 0.5f * (pp[q] - pm[q]);
+                    gT[2] = 0.5f * (pp[3] - pm[3]);
                 } else {
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const float xm = R0.f[q][ty + 1][tx];
-                        const float xp = wrapx ? F[q][(uint32_t)nx * (uint32_t)y + plane] : R0.f[q][ty + 1][tx + 2];
-                        const float ym = R0.f[q][ty][tx + 1];
-                        const float yp = wrapy ? F[q][(uint32_t)x + plane] : R0.f[q][ty + 2][tx + 1];
-                        if (q < 3) {
-                            du[0][q] = dval(xm, p0[q], xp, xlo, xhi, true, 0.f, true, 0.f);
-                            du[1][q] = dval(ym, p0[q], yp, ylo, yhi, true, 0.f, true, 0.f);
-                            du[2][q] = dval(pm[q], p0[q], pp[q], zlo, zhi, true, 0.f, true, 0.f);
-                        } else {
-                            gT[0] = dval(xm, p0[3], xp, xlo, xhi, dir[0], W.Tw[0], dir[1], W.Tw[1]);
-                            gT[1] = dval(ym, p0[3], yp, ylo, yhi, dir[2], W.Tw[2], dir[3], W.Tw[3]);
-                            gT[2] = dval(pm[3], p0[3], pp[3], zlo, zhi, dir[4], W.Tw[4], dir[5], W.Tw[5]);
-                        }
-                    }
+                    for (int q = 0; q < 3; ++q) du[2][q] = dval(pm[q], p0[q], pp[q], zlo, zhi, true, 0.f, true, 0.f);
+                    gT[2] = dval(pm[3], p0[3], pp[3], zlo, zhi, dir[4], W.Tw[4], dir[5], W.Tw[5]);
                 }
-                const float d = R0.d[ty][tx], u = p0[0], vv = p0[1], w = p0[2], t = p0[3];
+                const float d = d0, u = p0[0], vv = p0[1], w = p0[2], t = p0[3];
                 const float uu = u * u + vv * vv + w * w;
                 float eps = 0.f;
 #pragma unroll
@@ -308,31 +261,31 @@ __global__ void __launch_bounds__(kDiagThreads, 3) k_diag(const float *__restric
                 bs[8] += d; // sum rho = nodes + sum (rho - rho0)
                 umax2 = fmaxf(umax2, uu);
                 if (!(fabsf(uu) + fabsf(t) + fabsf(d) < INFINITY)) bad += 1; // a NaN or infinite moment
+                // Dirichlet faces: wall gradient -dT/dn (from the node and the
+                // next one inward) and anti-bounce-back link flux
+                // 2 g_in - (6 + a_T)/21 T_w; x and y faces summed per column
+                // (constant-index selects keep the wall tables out of local memory)
+                if (anydir && !fast) {
+                    if (fxc >= 0) {
+                        const bool lo = fxc == 0;
+                        wxa += (8.f * (lo ? W.Tw[0] : W.Tw[1]) - 9.f * p0[3] + tx1) * (1.f / 3.f);
+                        wxb += 2.f * mom[(5 + fxc) * s + n] - (lo ? P.abbT[0] : P.abbT[1]);
+                    }
+                    if (fyc >= 0) {
+                        const bool lo = fyc == 2;
+                        wya += (8.f * (lo ? W.Tw[2] : W.Tw[3]) - 9.f * p0[3] + ty1) * (1.f / 3.f);
+                        wyb += 2.f * mom[(5 + fyc) * s + n] - (lo ? P.abbT[2] : P.abbT[3]);
+                    }
+                }
             }
-            // Dirichlet faces: wall gradient -dT/dn (from the node and the next
-            // one inward) and anti-bounce-back link flux 2 g_in - (6 + a_T)/21 T_w;
-            // x and y faces summed per column, z faces (a whole plane) per warp
-            if (!anydir || fast) continue; // no face node in this warp
-            // (constant-index selects keep the wall tables out of local memory)
-            if (fxc >= 0) {
-                const bool lo = fxc == 0;
-                const float t1 = R0.f[3][ty + 1][lo ? tx + 2 : tx];
-                wxa += (8.f * (lo ? W.Tw[0] : W.Tw[1]) - 9.f * p0[3] + t1) * (1.f / 3.f);
-                wxb += 2.f * mom[(5 + fxc) * s + c + plane] - (lo ? P.abbT[0] : P.abbT[1]);
-            }
-            if (fyc >= 0) {
-                const bool lo = fyc == 2;
-                const float t1 = R0.f[3][lo ? ty + 2 : ty][tx + 1];
-                wya += (8.f * (lo ? W.Tw[2] : W.Tw[3]) - 9.f * p0[3] + t1) * (1.f / 3.f);
-                wyb += 2.f * mom[(5 + fyc) * s + c + plane] - (lo ? P.abbT[2] : P.abbT[3]);
-            }
-            const int fzc = perz ? -1 : (zlo && dir[4]) ? 4 : (zhi && dir[5]) ? 5 : -1; // uniform
+            // z faces (a whole plane): per warp, then shared FP64 sums
+            const int fzc = perz || !anydir ? -1 : (zlo && dir[4]) ? 4 : (zhi && dir[5]) ? 5 : -1; // uniform
             if (fzc >= 0) {
                 const bool lo = fzc == 4;
                 float ta = 0.f, tb = 0.f;
                 if (col) {
                     ta = (8.f * (lo ? W.Tw[4] : W.Tw[5]) - 9.f * p0[3] + (lo ? pp[3] : pm[3])) * (1.f / 3.f);
-                    tb = 2.f * mom[(5 + fzc) * s + c + plane] - (lo ? P.abbT[4] : P.abbT[5]);
+                    tb = 2.f * mom[(5 + fzc) * s + pz + c] - (lo ? P.abbT[4] : P.abbT[5]);
                 }
                 const DF da = df_warp_sum({ta, 0.f}), db = df_warp_sum({tb, 0.f});
                 if ((threadIdx.x & 31) == 0) {
@@ -340,11 +293,19 @@ __global__ void __launch_bounds__(kDiagThreads, 3) k_diag(const float *__restric
                     atomicAdd(&wall[6 + fzc], df_value(db));
                 }
             }
+            // march: planes z, z + 1, z + 2 become z - 1, z, z + 1
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                pm[q] = p0[q];
+                p0[q] = pp[q];
+                pp[q] = nn[q];
+            }
+            d0 = dn;
         }
         // the column's sums into the thread's totals; its x and y wall terms
         // into the shared FP64 sums
 #pragma unroll
-        for (int k = 0; k < 9; ++k) tot[k] += bs[k];
+        for (int k = 0; k < 9; ++k) tot[k][threadIdx.x] += bs[k];
         if (fxc >= 0) {
             atomicAdd(&wall[fxc], (double)wxa);
             atomicAdd(&wall[6 + fxc], (double)wxb);
@@ -353,8 +314,6 @@ __global__ void __launch_bounds__(kDiagThreads, 3) k_diag(const float *__restric
             atomicAdd(&wall[fyc], (double)wya);
             atomicAdd(&wall[6 + fyc], (double)wyb);
         }
-        cp_wait<0>();
-        __syncthreads(); // the ring is refilled by the next brick
     }
     const float vmax = sqrtf(umax2);
     // block reduction: double-float warp sums, FP64 across the warps
@@ -362,7 +321,7 @@ __global__ void __launch_bounds__(kDiagThreads, 3) k_diag(const float *__restric
     constexpr int slot[10] = {0, 1, 2, 3, 4, 5, 6, 7, 14, 15};
 #pragma unroll
     for (int k = 1; k < 10; ++k) {
-        const DF r = df_warp_sum({tot[k - 1], 0.f});
+        const DF r = df_warp_sum({tot[k - 1][threadIdx.x], 0.f});
         if (lane == 0) sh[wid][slot[k]] = df_value(r);
     }
     count = __reduce_add_sync(0xffffffffu, count);
@@ -403,29 +362,38 @@ __global__ void __launch_bounds__(kDiagThreads, 3) k_diag(const float *__restric
     }
 }
 
+// Sum of the blocks' partials: warp w takes the quantities w, w + 8, ...,
+// its lanes the blocks in turn (a fixed order, so the sums are reproducible),
+// then a shuffle tree.  FP64 arithmetic is slow on this GPU, so the
+// quantities run side by side in different warps rather than one after
+// another in one.
 __global__ void __launch_bounds__(kDiagThreads) k_diag_finish(const double *__restrict__ partial,
                                                               int nblocks, double *__restrict__ raw,
                                                               double *__restrict__ acc) {
-    __shared__ double sh[kDiagThreads / 32][kNDiag];
-    double v[kNDiag];
+    constexpr int nw = kDiagThreads / 32, per = (kNDiag + nw - 1) / nw;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    double v[per];
 #pragma unroll
-    for (int k = 0; k < kNDiag; ++k) v[k] = 0.0;
-    for (int bidx = threadIdx.x; bidx < nblocks; bidx += blockDim.x) {
+    for (int i = 0; i < per; ++i) v[i] = 0.0;
+    for (int b = lane; b < nblocks; b += 32) {
 #pragma unroll
-        for (int k = 0; k < kNDiag; ++k) {
-            const double p = partial[(int64_t)bidx * kNDiag + k];
-            v[k] = k == 16 ? fmax(v[k], p) : v[k] + p;
+        for (int i = 0; i < per; ++i) {
+            const int k = wid + nw * i;
+            if (k >= kNDiag) continue;
+            const double p = partial[(int64_t)b * kNDiag + k];
+            v[i] = k == 16 ? fmax(v[i], p) : v[i] + p;
         }
     }
-    block_reduce(v, sh);
-    if (threadIdx.x == 0) {
 #pragma unroll
-        for (int k = 0; k < kNDiag; ++k) {
-            raw[k] = v[k];
-            acc[k] = k == 16 ? fmax(acc[k], v[k]) : acc[k] + v[k];
+    for (int i = 0; i < per; ++i) {
+        const int k = wid + nw * i;
+        const double r = k == 16 ? warp_max(v[i]) : warp_sum(v[i]);
+        if (lane == 0 && k < kNDiag) {
+            raw[k] = r;
+            acc[k] = k == 16 ? fmax(acc[k], r) : acc[k] + r;
         }
-        acc[kNDiag] += 1.0;
     }
+    if (threadIdx.x == 0) acc[kNDiag] += 1.0;
 }
 
 // Local dissipation rates (Sec. 4): eps_u = nu/2 sum_ij (d_i u_j + d_j u_i)^2
