@@ -241,7 +241,8 @@ def run_judged(Ra, Pr, pred, coarse_up, stream, probe=2000, fallback=0.5, tol=1e
             lat.close()
 
 
-def evaluate(trainer, test_pairs, coarse, stream, log):
+def evaluate(trainer, test_pairs, coarse, stream, log, starts=("network", "coarse", "judged")):
+    """Steps to the steady state from rest and from each requested start."""
     results = []
     for k, (Ra, Pr) in enumerate(test_pairs):
         c = coarse[k]
@@ -252,15 +253,20 @@ def evaluate(trainer, test_pairs, coarse, stream, log):
         pred = trainer.predict(x)
         up = upsample(c).cpu().numpy()
         cold = run_from(Ra, Pr, None, stream)
-        warm = run_from(Ra, Pr, pred, stream)
-        interp = run_from(Ra, Pr, up, stream)
-        judged = run_judged(Ra, Pr, pred, up, stream)
-        results.append(dict(Ra=Ra, Pr=Pr, cold=cold, network=warm, upsampled_coarse=interp, judged=judged,
-                            speedup_network=cold["steps"] / max(warm["steps"], 1),
-                            speedup_judged=cold["steps"] / max(judged["steps"], 1),
-                            speedup_coarse=cold["steps"] / max(interp["steps"], 1)))
-        log(f"test {k}: Ra {Ra:.3g} Pr {Pr:.2f} cold {cold['steps']} network {warm['steps']} "
-            f"coarse {interp['steps']} judged {judged['steps']} ({judged['chosen']}) Nu {cold['Nu']:.5f}/{judged['Nu']:.5f}")
+        r = dict(Ra=Ra, Pr=Pr, cold=cold)
+        if "network" in starts:
+            r["network"] = run_from(Ra, Pr, pred, stream)
+            r["speedup_network"] = cold["steps"] / max(r["network"]["steps"], 1)
+        if "coarse" in starts:
+            r["upsampled_coarse"] = run_from(Ra, Pr, up, stream)
+            r["speedup_coarse"] = cold["steps"] / max(r["upsampled_coarse"]["steps"], 1)
+        if "judged" in starts:
+            r["judged"] = run_judged(Ra, Pr, pred, up, stream)
+            r["speedup_judged"] = cold["steps"] / max(r["judged"]["steps"], 1)
+        results.append(r)
+        log(f"test {k}: Ra {Ra:.3g} Pr {Pr:.2f} cold {cold['steps']} Nu {cold['Nu']:.5f} " +
+            " ".join(f"{key} {r[key]['steps']} (Nu {r[key]['Nu']:.5f})"
+                     for key in ("network", "upsampled_coarse", "judged") if key in r))
     return results
 
 
@@ -275,6 +281,7 @@ def summarize(results):
 
 
 def main():
+    global FINE
     import torch
 
     ap = argparse.ArgumentParser()
@@ -285,7 +292,11 @@ def main():
     ap.add_argument("--out", default="warmstart_report.json")
     ap.add_argument("--weights", default=None, help="save the trained BF16 weights (npz)")
     ap.add_argument("--load", default=None, help="evaluate stored weights instead of training")
+    ap.add_argument("--fine", type=int, default=FINE, help="edge of the fine lattice (the network's output)")
+    ap.add_argument("--starts", default="network,coarse,judged",
+                    help="warm starts to evaluate against the cold start (comma-separated)")
     args = ap.parse_args()
+    FINE = args.fine
     t0 = time.time()
     log = lambda m: print(f"[{time.time() - t0:7.1f}s] {m}", flush=True)  # noqa: E731
     stream = torch.cuda.Stream()
@@ -300,7 +311,7 @@ def main():
             trainer = Trainer(seed=1)
             trainer.load(args.load)
             report["weights"] = args.load
-            results = evaluate(trainer, test_pairs, cf, stream, log)
+            results = evaluate(trainer, test_pairs, cf, stream, log, starts=args.starts.split(","))
         else:
             log(f"coarse solves: {len(train_pairs) + len(test_pairs)}")
             cf, cs, cc, _ = steady_set(train_pairs + test_pairs, COARSE, stream)
@@ -321,7 +332,8 @@ def main():
             del xs, ys
             if args.weights:
                 trainer.save(args.weights)
-            results = evaluate(trainer, test_pairs, cf[len(train_pairs):], stream, log)
+            results = evaluate(trainer, test_pairs, cf[len(train_pairs):], stream, log,
+                               starts=args.starts.split(","))
         report["tests"] = results
         report["summary"] = summarize(results)
         report["wall_seconds"] = round(time.time() - t0, 1)
