@@ -928,7 +928,8 @@ lbm_status build_tiles(lbm_batch *b, int block, int span) {
         const uint32_t nr = (uint32_t)((warps + block / 32 - 1) / (block / 32));
         for (uint32_t k = 0; k < nr; k += sp) rows.push_back({c, TILE_ROWS, k, nr - k < sp ? nr - k : sp});
         // the row tiles cover the x faces of their rows; the y/z-face nodes remain
-        const uint32_t nf = (x->nface_yz + block - 1) / block;
+        const uint32_t fb = (uint32_t)(face_nodes_per_thread(b->storage) * block); // face nodes per block
+        const uint32_t nf = (x->nface_yz + fb - 1) / fb;
         for (uint32_t k = 0; k < nf; k += sp) faces.push_back({c, TILE_FACE, k, nf - k < sp ? nf - k : sp});
     }
     const size_t bytes = (even.size() + rows.size() + faces.size()) * sizeof(Tile);

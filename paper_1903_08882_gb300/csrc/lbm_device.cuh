@@ -643,4 +643,109 @@ __device__ __forceinline__ void odd_step_node(SEF<S> *__restrict__ f, SEG<S> *__
     if (MOM) write_sample(mom, s, n, m, b, g0);
 }
 
+// Face nodes per thread of the face kernel: one with FP32 storage, two with
+// the 2-byte storages (odd_step_node2).
+template <int S> constexpr int kFacePer = S == ST_F32 ? 1 : 2;
+
+// The same update for two nodes at once, na in the .x and nb in the .y
+// component, so that the collision runs on float2 values with the packed
+// FP32 instructions; vb = false leaves nb out (its lane recomputes na and
+// stores nothing).  The loads and stores take one node at a time, so that
+// only one node's neighbour descriptor is live.
+template <int S, bool MOM, int K>
+__device__ __forceinline__ void odd_load_one(const SEF<S> *__restrict__ f, const SEG<S> *__restrict__ g,
+                                             const Geom &G, const Phys &P, uint32_t n, float2 (&fl)[19],
+                                             float2 (&gl)[7]) {
+    const int64_t s = G.stride;
+    int x, y, z;
+    node_xyz(G, n, x, y, z);
+    const Nbr b = neighbours(G, x, y, z);
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        const int ex = ex19(i), ey = ey19(i), ez = ez19(i);
+        const float v = Store<FS(S)>::ld(src_wall(b, ex, ey, ez) ? f + i * s + n
+                                                                 : f + opp19(i) * s + (int64_t)n + src_off(b, ex, ey, ez));
+        if (K == 0) fl[i].x = v;
+        else fl[i].y = v;
+    }
+#pragma unroll
+    for (int i = 0; i < 7; ++i) {
+        const int ex = ex7(i), ey = ey7(i), ez = ez7(i);
+        const bool w = src_wall(b, ex, ey, ez);
+        float v = Store<GS(S)>::ld(w ? g + i * s + n : g + opp7(i) * s + (int64_t)n + src_off(b, ex, ey, ez));
+        if (i > 0 && w) { // a link through a Dirichlet face: anti-bounce-back
+            const int fc = face_of(-ex, -ey, -ez);
+            if ((P.dir_mask >> fc) & 1) v = P.abbT[fc] - v;
+        }
+        if (K == 0) gl[i].x = v;
+        else gl[i].y = v;
+    }
+}
+template <int S, int K>
+__device__ __forceinline__ void odd_store_one(SEF<S> *__restrict__ f, SEG<S> *__restrict__ g, const Geom &G,
+                                              const Phys &P, uint32_t n, const float2 (&fl)[19],
+                                              const float2 (&gl)[7]) {
+    const int64_t s = G.stride;
+    int x, y, z;
+    node_xyz(G, n, x, y, z);
+    const Nbr b = neighbours(G, x, y, z);
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        const int ex = ex19(i), ey = ey19(i), ez = ez19(i);
+        Store<FS(S)>::st(dst_wall(b, ex, ey, ez) ? f + opp19(i) * s + n
+                                                 : f + i * s + (int64_t)n + dst_off(b, ex, ey, ez),
+                         K == 0 ? fl[i].x : fl[i].y);
+    }
+    const uint32_t r = SRG(S) ? rnd_node(n, P.t) : 0u;
+    Store<GS(S)>::sts(g + n, K == 0 ? gl[0].x : gl[0].y, rnd_pop(r, 0));
+#pragma unroll
+    for (int i = 1; i < 7; ++i) {
+        const int ex = ex7(i), ey = ey7(i), ez = ez7(i);
+        const int fc = face_of(ex, ey, ez);
+        const bool w = dst_wall(b, ex, ey, ez);
+        const float u = K == 0 ? gl[i].x : gl[i].y;
+        const float v = w && ((P.dir_mask >> fc) & 1) ? P.abbT[fc] - u : u;
+        Store<GS(S)>::sts(w ? g + opp7(i) * s + n : g + i * s + (int64_t)n + dst_off(b, ex, ey, ez), v, rnd_pop(r, i));
+    }
+}
+
+template <int S, bool MOM>
+__device__ __forceinline__ void odd_step_node2(SEF<S> *__restrict__ f, SEG<S> *__restrict__ g, const Geom &G,
+                                               const Phys &P, float *__restrict__ mom, uint32_t na, uint32_t nb,
+                                               bool vb) {
+    if (!vb) nb = na;
+    float2 fl[19], gl[7];
+    odd_load_one<S, MOM, 0>(f, g, G, P, na, fl, gl);
+    odd_load_one<S, MOM, 1>(f, g, G, P, nb, fl, gl);
+    float2 g0[7];
+#pragma unroll
+    for (int i = 0; i < 7; ++i) g0[i] = gl[i];
+    const MacroT<float2> m = collide(P, fl, gl);
+    f = opaque(f);
+    g = opaque(g);
+    asm volatile("" : "+r"(na), "+r"(nb));
+    odd_store_one<S, 0>(f, g, G, P, na, fl, gl);
+    if (vb) odd_store_one<S, 1>(f, g, G, P, nb, fl, gl);
+    if (MOM) {
+        const int64_t s = G.stride;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            if (k == 1 && !vb) break;
+            const uint32_t n = k ? nb : na;
+            Macro mk;
+            mk.drho = k ? m.drho.y : m.drho.x;
+            mk.u = k ? m.u.y : m.u.x;
+            mk.v = k ? m.v.y : m.v.x;
+            mk.w = k ? m.w.y : m.w.x;
+            mk.T = k ? m.T.y : m.T.x;
+            float gk[7];
+#pragma unroll
+            for (int i = 0; i < 7; ++i) gk[i] = k ? g0[i].y : g0[i].x;
+            int x, y, z;
+            node_xyz(G, n, x, y, z);
+            write_sample(mom, s, n, mk, neighbours(G, x, y, z), gk);
+        }
+    }
+}
+
 } // namespace lbm

@@ -49,6 +49,8 @@ struct StepArgs {
 cudaError_t launch_step(const StepArgs &a);
 // AA odd step of the listed face nodes face[0 .. count) (general path).
 cudaError_t launch_face(const StepArgs &a, uint32_t count);
+// Face nodes each thread of the face kernel updates for a storage format.
+int face_nodes_per_thread(int storage);
 // Staged AA step (no diagnostic sample): even step, or odd step with the
 // face nodes through launch_face.
 cudaError_t launch_staged(const StepArgs &a);

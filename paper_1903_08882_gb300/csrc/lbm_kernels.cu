@@ -139,18 +139,30 @@ __global__ void __launch_bounds__(256, 3) k_aa_odd_interior(SEF<S> *__restrict__
     }
 }
 
-// Nodes next to a face, listed in `list`.
+// Nodes next to a face, listed in `list`.  With the 2-byte storages two per
+// thread (a warp takes 64 consecutive entries, lane l the entries l and
+// l + 32), so that the collision runs on the packed FP32 instructions: the
+// FP16 odd step at 257^3 is 4% shorter.  With FP32 one per thread: the two-node
+// form needs more than 128 registers there and gains nothing (small cells
+// lose 1%).  A block covers kFacePer<S> * bdim entries.
 template <int S, bool MOM>
 __device__ __forceinline__ void k_aa_odd_face_tile(SEF<S> *__restrict__ f, SEG<S> *__restrict__ g, const Geom &G,
                                                         const Phys &P, float *__restrict__ mom,
                                                         const uint32_t *__restrict__ list, uint32_t count, uint32_t blk, uint32_t tid, uint32_t bdim) {
-    const uint32_t t = blk * bdim + tid;
-    if (t >= count) return;
-    odd_step_node<S, MOM>(f, g, G, P, mom, list[t]);
+    if (kFacePer<S> == 1) {
+        const uint32_t t = blk * bdim + tid;
+        if (t >= count) return;
+        odd_step_node<S, MOM>(f, g, G, P, mom, list[t]);
+    } else {
+        const uint32_t a = 2u * (blk * bdim + (tid & ~31u)) + (tid & 31u);
+        if (a >= count) return;
+        const bool vb = a + 32u < count;
+        odd_step_node2<S, MOM>(f, g, G, P, mom, list[a], vb ? list[a + 32u] : 0u, vb);
+    }
 }
 
 template <int S, bool MOM>
-__global__ void __launch_bounds__(256, 3) k_aa_odd_face(SEF<S> *__restrict__ f, SEG<S> *__restrict__ g, Geom G,
+__global__ void __launch_bounds__(256, kFacePer<S> == 1 ? 3 : 2) k_aa_odd_face(SEF<S> *__restrict__ f, SEG<S> *__restrict__ g, Geom G,
                                                         Phys P, float *__restrict__ mom,
                                                         const uint32_t *__restrict__ list, uint32_t count) {
     k_aa_odd_face_tile<S, MOM>(f, g, G, P, mom, list, count, blockIdx.x, threadIdx.x, blockDim.x);
@@ -698,7 +710,7 @@ static cudaError_t step_t(const StepArgs &a) {
         } else {
             // the row kernel covers the x faces of its rows; the listed y/z-face nodes remain
             const unsigned nwarps = a.G.cpp * (unsigned)(a.G.nz - 2);
-            const unsigned ni = blocks_for(nwarps, a.block / 32), nf = blocks_for(a.nface_yz, a.block);
+            const unsigned ni = blocks_for(nwarps, a.block / 32), nf = blocks_for(a.nface_yz, kFacePer<S> * a.block);
             if (a.mom) {
                 if (ni) k_aa_odd_rows<S, true><<<ni, a.block, 0, a.stream>>>(f, g, a.G, a.P, a.mom);
                 if (nf) k_aa_odd_face<S, true><<<nf, a.block, 0, a.stream>>>(f, g, a.G, a.P, a.mom, a.face, a.nface_yz);
@@ -713,7 +725,7 @@ static cudaError_t step_t(const StepArgs &a) {
             if (a.mom) k_aa_even<S, true><<<nb, a.block, 0, a.stream>>>(f, g, a.G, a.P, a.mom);
             else k_aa_even<S, false><<<nb, a.block, 0, a.stream>>>(f, g, a.G, a.P, nullptr);
         } else {
-            const unsigned ni = blocks_for(a.G.ni, a.block), nf = blocks_for(a.nface, a.block);
+            const unsigned ni = blocks_for(a.G.ni, a.block), nf = blocks_for(a.nface, kFacePer<S> * a.block);
             if (a.mom) {
                 if (ni) k_aa_odd_interior<S, true><<<ni, a.block, 0, a.stream>>>(f, g, a.G, a.P, a.mom);
                 if (nf) k_aa_odd_face<S, true><<<nf, a.block, 0, a.stream>>>(f, g, a.G, a.P, a.mom, a.face, a.nface);
@@ -734,10 +746,12 @@ static cudaError_t step_t(const StepArgs &a) {
 
 template <int S> static cudaError_t face_t(const StepArgs &a, uint32_t count) {
     if (count)
-        k_aa_odd_face<S, false><<<blocks_for(count, 256), 256, 0, a.stream>>>(
+        k_aa_odd_face<S, false><<<blocks_for(count, kFacePer<S> * 256), 256, 0, a.stream>>>(
             static_cast<SEF<S> *>(a.f), static_cast<SEG<S> *>(a.g), a.G, a.P, nullptr, a.face, count);
     return cudaGetLastError();
 }
+
+int face_nodes_per_thread(int storage) { return storage == ST_F32 ? kFacePer<ST_F32> : kFacePer<ST_F16>; }
 
 cudaError_t launch_face(const StepArgs &a, uint32_t count) {
     switch (a.storage) {
