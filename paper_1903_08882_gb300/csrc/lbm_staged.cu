@@ -395,8 +395,9 @@ __device__ __forceinline__ void update_pair(SF<S> *f, SG<S> *g, const Geom &G, c
 // into registers and arrives on the stage's "empty" barrier (one arrival per
 // compute warp) before it updates the nodes; warp 0 refills a stage once
 // its empty barrier has completed.  On an odd step warp 0 only issues copies;
-// on an even step it also computes and refills the stage of each tile after
-// updating its own nodes of it.  No block-wide barrier is taken per tile: a
+// on an even step it also computes, and refills the stage of each tile once
+// every warp has read it, before updating its own nodes of it.  No
+// block-wide barrier is taken per tile: a
 // bulk copy's operands come from uniform registers, so a warp issues its
 // lanes' copies one after another, and with a block barrier every warp
 // waited for that serial issue each tile (a third of the time of a tile).
