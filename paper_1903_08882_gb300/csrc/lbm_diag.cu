@@ -95,15 +95,24 @@ struct KSum {
     __device__ __forceinline__ DF df() const { return {s, -c}; }
 };
 
-// Derivative from the values at the node and its two neighbours along an
-// axis, with the stencils of deriv(): wm / wp flag a wall behind the -1 / +1
-// neighbour, vlo / vhi a known wall value wlo / whi there.
-__device__ __forceinline__ float dval(float pm, float p0, float pp, bool wm, bool wp, bool vlo, float wlo, bool vhi,
-                                      float whi) {
-    if (!wm && !wp) return 0.5f * (pp - pm);
-    if (wm && wp) return 0.f;
-    if (wm) return vlo ? (-4.f / 3.f) * wlo + p0 + pp * (1.f / 3.f) : 0.5f * (pp - p0);
-    return vhi ? (4.f / 3.f) * whi - p0 - pm * (1.f / 3.f) : 0.5f * (p0 - pm);
+// Derivative along an axis from the values at the node and its two
+// neighbours, with the stencils of the file header (wm / wp: a wall behind
+// the -1 / +1 neighbour; vlo / vhi: a known wall value wlo / whi there), as
+// coefficients d = m phi_-1 + o phi_0 + p phi_+1 + k chosen per node with
+// selects rather than branches (the lanes of a warp next to a wall take
+// different stencils).
+struct Coef {
+    float m, o, p, k;
+};
+__device__ __forceinline__ Coef coef(bool wm, bool wp, bool vlo, float wlo, bool vhi, float whi) {
+    Coef c = {-0.5f, 0.f, 0.5f, 0.f};
+    if (wm && wp) c = {0.f, 0.f, 0.f, 0.f};
+    else if (wm) c = vlo ? Coef{0.f, 1.f, 1.f / 3.f, (-4.f / 3.f) * wlo} : Coef{0.f, -0.5f, 0.5f, 0.f};
+    else if (wp) c = vhi ? Coef{-1.f / 3.f, -1.f, 0.f, (4.f / 3.f) * whi} : Coef{-0.5f, 0.5f, 0.f, 0.f};
+    return c;
+}
+__device__ __forceinline__ float apply(const Coef &c, float pm, float p0, float pp) {
+    return fmaf(c.m, pm, fmaf(c.o, p0, fmaf(c.p, pp, c.k)));
 }
 
 // Diagnostic sums of one sample.  The lattice is cut into columns of
@@ -212,18 +221,20 @@ __global__ void __launch_bounds__(kDiagThreads, 3) k_diag(const float *__restric
                     float vm[4], vp[4];
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        vm[q] = F[q][n + om];
-                        vp[q] = F[q][n + op];
+                        const float *fq = F[q] + n; // 32-bit neighbour offsets from the node's own address
+                        vm[q] = fq[om];
+                        vp[q] = fq[op];
                     }
                     if (fast) {
 #pragma unroll
                         for (int q = 0; q < 3; ++q) du[a][q] = 0.5f * (vp[q] - vm[q]);
                         gT[a] = 0.5f * (vp[3] - vm[3]);
                     } else {
+                        const Coef cv = coef(wlo, whi, true, 0.f, true, 0.f);
+                        const Coef ct = coef(wlo, whi, dir[2 * a], W.Tw[2 * a], dir[2 * a + 1], W.Tw[2 * a + 1]);
 #pragma unroll
-                        for (int q = 0; q < 3; ++q) du[a][q] = dval(vm[q], p0[q], vp[q], wlo, whi, true, 0.f, true, 0.f);
-                        gT[a] = dval(vm[3], p0[3], vp[3], wlo, whi, dir[2 * a], W.Tw[2 * a], dir[2 * a + 1],
-                                     W.Tw[2 * a + 1]);
+                        for (int q = 0; q < 3; ++q) du[a][q] = apply(cv, vm[q], p0[q], vp[q]);
+                        gT[a] = apply(ct, vm[3], p0[3], vp[3]);
                     }
                     const float t1 = (a == 0 ? fxc == 0 : fyc == 2) ? vp[3] : vm[3];
                     if (a == 0) tx1 = t1;
@@ -234,9 +245,11 @@ __global__ void __launch_bounds__(kDiagThreads, 3) k_diag(const float *__restric
                     for (int q = 0; q < 3; ++q) du[2][q] = 0.5f * (pp[q] - pm[q]);
                     gT[2] = 0.5f * (pp[3] - pm[3]);
                 } else {
+                    const Coef cv = coef(zlo, zhi, true, 0.f, true, 0.f);
+                    const Coef ct = coef(zlo, zhi, dir[4], W.Tw[4], dir[5], W.Tw[5]);
 #pragma unroll
-                    for (int q = 0; q < 3; ++q) du[2][q] = dval(pm[q], p0[q], pp[q], zlo, zhi, true, 0.f, true, 0.f);
-                    gT[2] = dval(pm[3], p0[3], pp[3], zlo, zhi, dir[4], W.Tw[4], dir[5], W.Tw[5]);
+                    for (int q = 0; q < 3; ++q) du[2][q] = apply(cv, pm[q], p0[q], pp[q]);
+                    gT[2] = apply(ct, pm[3], p0[3], pp[3]);
                 }
                 const float d = d0, u = p0[0], vv = p0[1], w = p0[2], t = p0[3];
                 const float uu = u * u + vv * vv + w * w;
