@@ -122,6 +122,34 @@ def test_random_state_steps(lbm, walls, scheme, n):
         assert (e < 2e-6).all(), e
 
 
+@pytest.mark.parametrize("storage", ["fp16s", "fp16m"])
+@pytest.mark.parametrize("walls", list(WALLS))
+@pytest.mark.parametrize("n", [(5, 6, 7), (13, 11, 12), (3, 3, 3), (45, 37, 13), (97, 41, 23), (17, 45, 5),
+                               (20, 3, 40)])
+def test_staged_reduced_storage_random_states(lbm, walls, storage, n):
+    """The staged kernels with the 2-byte storages, whose odd step leaves the
+    y/z-face nodes (every face node for rows shorter than 16 nodes) to the
+    face kernel, on every wall set.  Shapes from a single tile (most blocks
+    get none) to several tiles per plane and rows shorter than 16 nodes; four steps
+    (two odd) from a random state against the register kernels with the
+    same storage (same roundings and random bits: agreement to the last bit
+    of the 11-bit significand but for multiply-add contraction, 2e-3) and
+    against the oracle (one storage rounding per step, 4e-3)."""
+    p = _orc_params(n, WALLS[walls])
+    f0, g0 = _random_state(p, 5)
+    out = []
+    for pipe in ("register", "staged"):
+        with _lattice(lbm, n, WALLS[walls], storage=storage, nodes_per_thread=2, pipeline=pipe) as lat:
+            lat.set_populations(f0, g0)
+            lat.step(4)
+            out.append(lat.populations())
+    fo, go = oracle.run(p, f0, g0, 4)
+    ef, eg = _rel_pop(*out[1], *out[0])
+    assert ef < 2e-3 and eg < 2e-3, (ef, eg)
+    ef, eg = _rel_pop(*out[1], fo, go)
+    assert ef < 4e-3 and eg < 4e-3, (ef, eg)
+
+
 def test_shared_state_one_step_cfg1(lbm):
     """Side-heated 33^3, Ra=1e4, Pr=0.71: the oracle state after 500 steps from
     rest, loaded into the library; one and two steps."""
