@@ -47,7 +47,15 @@ struct StepArgs {
 };
 
 cudaError_t launch_step(const StepArgs &a);
-// AA odd step of the listed face nodes face[0 .. count) (general path).
+// Launch `fn` as a programmatic dependent launch: its blocks may be
+// scheduled while the kernel before it in the stream finishes, once every
+// block of that one has signalled (griddepcontrol.launch_dependents); the
+// kernel itself waits for the one before it (griddepcontrol.wait) before it
+// touches memory, so the order of the data is that of ordinary launches and
+// only the launch and block set-up overlap.
+cudaError_t pdl_launch(const void *fn, int grid, int block, int smem, cudaStream_t stream, void **args);
+// AA odd step of the listed face nodes face[0 .. count) (general path),
+// after the staged odd kernel.
 cudaError_t launch_face(const StepArgs &a, uint32_t count);
 // Face nodes each thread of the face kernel updates for a storage format.
 int face_nodes_per_thread(int storage);

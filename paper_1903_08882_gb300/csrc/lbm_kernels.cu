@@ -744,11 +744,29 @@ static cudaError_t step_t(const StepArgs &a) {
     return cudaGetLastError();
 }
 
+// The face kernel after the staged odd kernel: a programmatic dependent
+// launch (see pdl_launch), waiting for that kernel before it reads.
+template <int S>
+__global__ void __launch_bounds__(256, kFacePer<S> == 1 ? 3 : 2) k_aa_odd_face_pdl(SEF<S> *__restrict__ f,
+                                                                                  SEG<S> *__restrict__ g, Geom G,
+                                                                                  Phys P,
+                                                                                  const uint32_t *__restrict__ list,
+                                                                                  uint32_t count) {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    k_aa_odd_face_tile<S, false>(f, g, G, P, nullptr, list, count, blockIdx.x, threadIdx.x, blockDim.x);
+}
+
 template <int S> static cudaError_t face_t(const StepArgs &a, uint32_t count) {
-    if (count)
-        k_aa_odd_face<S, false><<<blocks_for(count, kFacePer<S> * 256), 256, 0, a.stream>>>(
-            static_cast<SEF<S> *>(a.f), static_cast<SEG<S> *>(a.g), a.G, a.P, nullptr, a.face, count);
-    return cudaGetLastError();
+    if (!count) return cudaGetLastError();
+    SEF<S> *f = static_cast<SEF<S> *>(a.f);
+    SEG<S> *g = static_cast<SEG<S> *>(a.g);
+    Geom G = a.G;
+    Phys P = a.P;
+    const uint32_t *list = a.face;
+    void *args[] = {&f, &g, &G, &P, &list, &count};
+    return pdl_launch(reinterpret_cast<const void *>(&k_aa_odd_face_pdl<S>), blocks_for(count, kFacePer<S> * 256),
+                      256, 0, a.stream, args);
 }
 
 int face_nodes_per_thread(int storage) { return storage == ST_F32 ? kFacePer<ST_F32> : kFacePer<ST_F16>; }

@@ -429,6 +429,11 @@ __global__ void __launch_bounds__(kThreads, 2)
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();
+    // programmatic dependent launch: the next kernel's blocks may be
+    // scheduled as this one's retire, and this one reads nothing before the
+    // kernel before it has completed
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
 
     if (ODD && warp == 0) {
         int j = 0;
@@ -581,26 +586,42 @@ template <int S> cudaError_t staged_attr(int *blocks_per_sm) {
 }
 
 template <int S> cudaError_t staged_launch(const StepArgs &a) {
-    auto f = static_cast<SF<S> *>(a.f);
-    auto g = static_cast<SG<S> *>(a.g);
-    const StagedGeom &T = a.T;
-    if (a.parity == 0) {
-        k_aa_staged<S, false, false><<<T.grid, kThreads, Stage<S, false>::smem, a.stream>>>(f, g, a.G, a.P, T, a.err);
-        return cudaGetLastError();
-    }
-    constexpr int b = Stage<S, true>::smem;
+    SF<S> *f = static_cast<SF<S> *>(a.f);
+    SG<S> *g = static_cast<SG<S> *>(a.g);
+    Geom G = a.G;
+    Phys P = a.P;
+    StagedGeom T = a.T;
+    int *err = a.err;
+    void *args[] = {&f, &g, &G, &P, &T, &err};
+    if (a.parity == 0)
+        return pdl_launch(reinterpret_cast<const void *>(&k_aa_staged<S, false, false>), T.grid, kThreads,
+                          Stage<S, false>::smem, a.stream, args);
     if (T.odd_tiles) {
-        if (T.xf) k_aa_staged<S, true, true><<<T.grid, kThreads, b, a.stream>>>(f, g, a.G, a.P, T, a.err);
-        else k_aa_staged<S, true, false><<<T.grid, kThreads, b, a.stream>>>(f, g, a.G, a.P, T, a.err);
+        const void *fn = T.xf ? reinterpret_cast<const void *>(&k_aa_staged<S, true, true>)
+                              : reinterpret_cast<const void *>(&k_aa_staged<S, true, false>);
+        const cudaError_t e = pdl_launch(fn, T.grid, kThreads, Stage<S, true>::smem, a.stream, args);
+        if (e != cudaSuccess) return e;
     }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
     // the nodes next to a y or z face (and, for rows shorter than kXfMinNx,
     // those next to an x face) go through the general face kernel
     return launch_face(a, T.xf ? a.nface_yz : a.nface);
 }
 
 } // namespace
+
+cudaError_t pdl_launch(const void *fn, int grid, int block, int smem, cudaStream_t stream, void **args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, fn, args);
+}
 
 int staged_tile_nodes(int odd) { return odd ? kTile<true> : kTile<false>; }
 
