@@ -180,6 +180,30 @@ lbm_status lbm_get_constants(const lbm_ctx *ctx, lbm_constants *out);
  * step counter is kept; time averages are not touched. */
 lbm_status lbm_set_fields(lbm_ctx *ctx, const double *rho, const double *u3, const double *T);
 
+/* The state replacement of lbm_set_fields in two asynchronous halves, so that
+ * the host-to-device copy of the next fields overlaps the steps that run
+ * before they are needed (AA streaming only; LBM_ERR_PARAM otherwise).
+ *
+ * lbm_upload_fields queues the copy of host fields rho[n], u3[3][n], T[n]
+ * (n = nx ny nz, x fastest) into a device staging buffer of 5 n doubles that
+ * the context owns (allocated at the first call, through the context's
+ * allocator) on a copy stream of its own, and returns at once.  The copy
+ * waits for the kernel of the previous lbm_apply_fields, so the buffer is
+ * never overwritten while it is read.  The host arrays must stay valid and
+ * unchanged until the copy has completed: until the next synchronising call
+ * (lbm_diagnostics, lbm_moments, lbm_synchronize, ...) after the
+ * lbm_apply_fields that uses them.  With pinned host memory the copy runs
+ * beside the context's kernels; with pageable memory cudaMemcpyAsync copies
+ * before it returns.
+ *
+ * lbm_apply_fields makes the context's stream wait for the last upload and
+ * then writes the equilibrium populations f^eq(rho, u), g^eq(T, u)
+ * (Sec. 2.2, 2.3) of the uploaded fields, as lbm_set_fields does, without
+ * synchronising.  The step counter is kept; time averages are not touched.
+ * LBM_ERR_STATE when no upload is pending (each upload is applied once). */
+lbm_status lbm_upload_fields(lbm_ctx *ctx, const double *rho, const double *u3, const double *T);
+lbm_status lbm_apply_fields(lbm_ctx *ctx);
+
 /* Replace the state by host populations f19[19][n], g7[7][n]: the
  * pre-collision populations f_i(x, t) of Eq. MRT and g_i(x, t) of Eq. MRT_T. */
 lbm_status lbm_set_populations(lbm_ctx *ctx, const double *f19, const double *g7);

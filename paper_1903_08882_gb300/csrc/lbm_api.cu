@@ -66,6 +66,13 @@ struct lbm_ctx {
     int block = 256;
     float *hstage = nullptr; // pinned host staging, grown on demand
     size_t hstage_bytes = 0;
+    // lbm_upload_fields / lbm_apply_fields: fields copied on their own stream
+    // into a device staging buffer (rho, u, v, w, T: n doubles each)
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_uploaded = nullptr, ev_consumed = nullptr;
+    double *fields = nullptr;
+    size_t fields_bytes = 0;
+    bool upload_pending = false, consumed_recorded = false;
     std::string err;
 
     float *host_stage(size_t bytes) {
@@ -275,6 +282,17 @@ lbm_status release(lbm_ctx *ctx) {
     if (ctx->hstage) cudaFreeHost(ctx->hstage);
     ctx->hstage = nullptr;
     ctx->hstage_bytes = 0;
+    if (ctx->copy_stream) {
+        cudaStreamSynchronize(ctx->copy_stream);
+        cudaStreamDestroy(ctx->copy_stream);
+    }
+    if (ctx->ev_uploaded) cudaEventDestroy(ctx->ev_uploaded);
+    if (ctx->ev_consumed) cudaEventDestroy(ctx->ev_consumed);
+    ctx->dfree(ctx->fields, ctx->fields_bytes);
+    ctx->copy_stream = nullptr;
+    ctx->ev_uploaded = ctx->ev_consumed = nullptr;
+    ctx->fields = nullptr;
+    ctx->fields_bytes = 0;
     return LBM_OK;
 }
 
@@ -497,6 +515,48 @@ const char *lbm_last_error(const lbm_ctx *ctx) {
 lbm_status lbm_get_constants(const lbm_ctx *ctx, lbm_constants *out) {
     if (!ctx || !out) return LBM_ERR_PARAM;
     *out = ctx->c;
+    return LBM_OK;
+}
+
+lbm_status lbm_upload_fields(lbm_ctx *ctx, const double *rho, const double *u3, const double *T) {
+    if (!ctx || !rho || !u3 || !T) return ctx ? fail(ctx, LBM_ERR_PARAM, "NULL array") : LBM_ERR_PARAM;
+    if (ctx->p.streaming != LBM_STREAM_AA) return fail(ctx, LBM_ERR_PARAM, "lbm_upload_fields needs AA streaming");
+    DeviceGuard dg(ctx->dev);
+    const size_t n = (size_t)ctx->c.nodes;
+    if (!ctx->copy_stream) {
+        CK(ctx, cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+        CK(ctx, cudaEventCreateWithFlags(&ctx->ev_uploaded, cudaEventDisableTiming));
+        CK(ctx, cudaEventCreateWithFlags(&ctx->ev_consumed, cudaEventDisableTiming));
+    }
+    if (!ctx->fields) {
+        ctx->fields = static_cast<double *>(ctx->dalloc(5 * n * sizeof(double)));
+        if (!ctx->fields) return fail(ctx, LBM_ERR_OOM, "field staging allocation failed");
+        ctx->fields_bytes = 5 * n * sizeof(double);
+    }
+    // the staging buffer may still feed the kernel of the last lbm_apply_fields
+    if (ctx->consumed_recorded) CK(ctx, cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_consumed, 0));
+    double *d = ctx->fields;
+    CK(ctx, cudaMemcpyAsync(d, rho, n * sizeof(double), cudaMemcpyHostToDevice, ctx->copy_stream));
+    CK(ctx, cudaMemcpyAsync(d + n, u3, 3 * n * sizeof(double), cudaMemcpyHostToDevice, ctx->copy_stream));
+    CK(ctx, cudaMemcpyAsync(d + 4 * n, T, n * sizeof(double), cudaMemcpyHostToDevice, ctx->copy_stream));
+    CK(ctx, cudaEventRecord(ctx->ev_uploaded, ctx->copy_stream));
+    ctx->upload_pending = true;
+    return LBM_OK;
+}
+
+lbm_status lbm_apply_fields(lbm_ctx *ctx) {
+    if (!ctx) return LBM_ERR_PARAM;
+    if (!ctx->upload_pending) return fail(ctx, LBM_ERR_STATE, "lbm_apply_fields: no fields uploaded since the last call");
+    DeviceGuard dg(ctx->dev);
+    const size_t n = (size_t)ctx->c.nodes;
+    double *d = ctx->fields;
+    CK(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_uploaded, 0));
+    CK(ctx, launch_fields_natural(ctx->p.storage, d, d + n, d + 4 * n, ctx->fbase(0), ctx->gbase(0), ctx->G,
+                                  ctx->P, ctx->stream));
+    CK(ctx, cudaEventRecord(ctx->ev_consumed, ctx->stream));
+    ctx->consumed_recorded = true;
+    ctx->upload_pending = false;
+    ctx->parity = 0;
     return LBM_OK;
 }
 

@@ -108,6 +108,8 @@ def lib():
         "lbm_last_error": ([c_void_p], ctypes.c_char_p),
         "lbm_get_constants": ([c_void_p, P(LbmConstants)], c_int),
         "lbm_set_fields": ([c_void_p, dp, dp, dp], c_int),
+        "lbm_upload_fields": ([c_void_p, dp, dp, dp], c_int),
+        "lbm_apply_fields": ([c_void_p], c_int),
         "lbm_set_populations": ([c_void_p, dp, dp], c_int),
         "lbm_get_populations": ([c_void_p, dp, dp], c_int),
         "lbm_get_populations_at": ([c_void_p, i64p, c_int64, dp, dp], c_int),
@@ -274,6 +276,23 @@ def lbm_set_fields(ctx, rho, u3, T, shape):
         u3 = u3.reshape(3, 1, 1, 1)
     r, u, t = _f64(rho, shape), _f64(u3, (3,) + tuple(shape)), _f64(T, shape)
     _check(ctx, lib().lbm_set_fields(ctx, _dp(r), _dp(u), _dp(t)))
+
+
+def lbm_upload_fields(ctx, rho, u3, T, shape):
+    """Queue the copy of the fields (marshalled as for lbm_set_fields) on the
+    context's copy stream.  Returns the marshalled arrays: the caller keeps
+    them alive until a synchronising call after the lbm_apply_fields that
+    uses them (the copy reads them asynchronously)."""
+    u3 = np.asarray(u3, dtype=np.float64)
+    if u3.ndim == 1:
+        u3 = u3.reshape(3, 1, 1, 1)
+    r, u, t = _f64(rho, shape), _f64(u3, (3,) + tuple(shape)), _f64(T, shape)
+    _check(ctx, lib().lbm_upload_fields(ctx, _dp(r), _dp(u), _dp(t)))
+    return r, u, t
+
+
+def lbm_apply_fields(ctx):
+    _check(ctx, lib().lbm_apply_fields(ctx))
 
 
 def lbm_set_populations(ctx, f19, g7):
@@ -494,6 +513,10 @@ class Lattice:
         self.shape = (nz, ny, nx)
         self.params = make_params(nx, ny, nz, walls, **kw)
         self.ctx = lbm_create(self.params, allocator=allocator, stream=stream)
+        # host fields of asynchronous uploads: not yet applied (their copies
+        # may run until an apply makes the stream wait for them), and applied
+        # (done once the stream has been synchronised)
+        self._uploaded, self._applied = [], []
 
     def close(self):
         if self.ctx is not None and self.ctx.value:
@@ -517,6 +540,18 @@ class Lattice:
     def set_fields(self, rho, u3, T):
         lbm_set_fields(self.ctx, rho, u3, T, self.shape)
 
+    def upload_fields(self, rho, u3, T):
+        """Asynchronous half of set_fields: the copy of the next fields runs
+        on the context's copy stream beside the steps queued meanwhile; the
+        arrays are kept here until a synchronising call after the
+        apply_fields that uses them."""
+        self._uploaded.append(lbm_upload_fields(self.ctx, rho, u3, T, self.shape))
+
+    def apply_fields(self):
+        lbm_apply_fields(self.ctx)
+        self._applied += self._uploaded
+        self._uploaded = []
+
     def set_populations(self, f, g):
         lbm_set_populations(self.ctx, f, g)
 
@@ -530,7 +565,9 @@ class Lattice:
         lbm_step(self.ctx, n)
 
     def moments(self):
-        return lbm_moments(self.ctx, self.shape)
+        out = lbm_moments(self.ctx, self.shape)
+        self._applied = []
+        return out
 
     def sample(self):
         lbm_sample(self.ctx)
@@ -542,10 +579,13 @@ class Lattice:
         return lbm_nusselt_profile(self.ctx, self.shape, axis)
 
     def diagnostics(self, reset=False, raise_on_diverged=True):
-        return lbm_diagnostics(self.ctx, reset, raise_on_diverged)
+        out = lbm_diagnostics(self.ctx, reset, raise_on_diverged)
+        self._applied = []
+        return out
 
     def synchronize(self):
         lbm_synchronize(self.ctx)
+        self._applied = []
 
     def set_wait_budget(self, cycles):
         lbm_set_wait_budget(self.ctx, cycles)

@@ -448,3 +448,45 @@ def test_full_size_257_sampled(lbm, storage, tol):
                 scale_f = max(scale_f, np.abs(fr - W19).max())
                 scale_g = max(scale_g, np.abs(gr).max())
             assert worst_f / scale_f < tol and worst_g / scale_g < tol, (k, worst_f / scale_f, worst_g / scale_g)
+
+
+@pytest.mark.parametrize("storage", ["fp32", "fp16s"])
+def test_upload_apply_fields_match_set_fields(lbm, storage):
+    """lbm_upload_fields + lbm_apply_fields build the same state as
+    lbm_set_fields, bit for bit, also when the next fields are uploaded on the
+    copy stream while the steps from the previous ones run (the pipelined
+    pattern of the end-to-end benchmark), on a side-heated and a
+    Rayleigh-Benard cell;
+    lbm_apply_fields with no pending upload is LBM_ERR_STATE and the pull
+    scheme refuses uploads with LBM_ERR_PARAM."""
+    n = (45, 37, 13)
+    sh = (n[2], n[1], n[0])
+    fields = [inputs.random_fields(sh, seed, du=0.02) for seed in (11, 12, 13)]
+    import torch
+
+    # pinned copies, so that the uploads run asynchronously
+    pin = [tuple(torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy() for a in f) for f in fields]
+    for walls in ("side_heated", "rayleigh_benard"):
+        out = []
+        with _lattice(lbm, n, WALLS[walls], storage=storage) as lat:
+            for rho, u, T in fields:
+                lat.set_fields(rho, u, T)
+                lat.step(7)
+            out.append(lat.populations())
+        with _lattice(lbm, n, WALLS[walls], storage=storage) as lat:
+            lat.upload_fields(*pin[0])
+            for k in range(3):
+                lat.apply_fields()
+                lat.step(7)
+                if k < 2:
+                    lat.upload_fields(*pin[k + 1])  # beside the steps just queued
+            out.append(lat.populations())
+            with pytest.raises(lbm.LbmError) as ei:
+                lat.apply_fields()
+            assert ei.value.status == lbm.LBM_ERR_STATE
+        for a, b in zip(out[0], out[1]):
+            assert np.array_equal(a, b)
+    with _lattice(lbm, n, WALLS["side_heated"], storage=storage, streaming="pull2") as lat:
+        with pytest.raises(lbm.LbmError) as ei:
+            lat.upload_fields(*fields[0])
+        assert ei.value.status == lbm.LBM_ERR_PARAM
