@@ -369,3 +369,34 @@ def test_run_log_records_a_steady_run(tmp_path):
     with drivers.RunLog(path) as log:
         log.write("note", text="resumed")
     assert len(drivers.read_log(path)) == len(recs) + 1
+
+
+def test_rb_ensemble_pools_the_samples(tmp_path):
+    """The ensemble reference script pools its members' samples: the mean of
+    the members' Nu (linear in the sampled sums) and the root mean square of
+    their Re equal the oracle's own finalisation of all samples' summed raw
+    diagnostics (equal sample counts).  Tiny cell: 8^3, two members of 100
+    samples."""
+    import importlib.util
+    import os
+
+    import oracle
+
+    here = os.path.dirname(os.path.abspath(__file__))
+    spec = importlib.util.spec_from_file_location("make_rb_ensemble", os.path.join(here, "golden", "make_rb_ensemble.py"))
+    ens = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(ens)
+    paths = [str(tmp_path / f"member_{k}.json") for k in range(2)]
+    for k, path in enumerate(paths):
+        ens.member((8, 1e6, 7.0, 1.0, 5.0, 4, 5 + k, path))
+    out = ens.combine(8, 1e6, 7.0, 4, paths)
+    assert out["samples"] == 100 and len(out["members"]) == 2 and len(out["series"][0]) == 10
+    import json
+
+    acc = sum(np.array(dict((n, a) for n, a in json.load(open(q))["snapshots"])[100]) for q in paths)
+    p = oracle.cell(8, 1e6, 7.0, oracle.rayleigh_benard_walls(), U=0.1)
+    d = oracle.finalize(p, acc / 200)
+    ref = dict(Nu_vol=d["Nu_vol"], Nu_wall=0.5 * (d["Nu_face"][4] - d["Nu_face"][5]), Nu_kin=d["Nu_kin"],
+               Nu_th=d["Nu_th"], Re_rms=d["Re_rms"], Re_w=d["Re_w"], E=d["E"])
+    for k, v in ref.items():
+        assert abs(out[k] - v) <= 1e-12 * max(1.0, abs(v)), (k, out[k], v)
