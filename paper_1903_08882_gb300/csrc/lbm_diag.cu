@@ -496,11 +496,32 @@ __global__ void __launch_bounds__(kDiagThreads) k_eps_hist(const float *__restri
         if (hs[i]) atomicAdd(&counts[i], (unsigned long long)hs[i]);
 }
 
+// Blocks for a grid-stride kernel over the nodes: as many as the device
+// holds at once at the kernel's own occupancy (its registers and shared
+// memory), at most max_per_sm per SM (each block flushes its partial sums
+// with global atomics once), no more than the nodes need.  (k_diag's brick
+// grid, which these kernels used before, is sized for k_diag's registers: at
+// 257^3 it left the PDF passes 16% slower.)
+static int resident_blocks(const void *fn, size_t smem, uint32_t n, int max_per_sm = 4) {
+    int dev = 0, nsm = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess || nsm < 1)
+        nsm = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, kDiagThreads, smem) != cudaSuccess || per < 1)
+        per = 1;
+    cudaGetLastError();
+    per = per < max_per_sm ? per : max_per_sm;
+    const int64_t need = ((int64_t)n + kDiagThreads - 1) / kDiagThreads;
+    const int64_t cap = (int64_t)per * nsm;
+    return (int)(need < cap ? need : cap);
+}
+
 cudaError_t launch_eps_sq(const float *mom, const Geom &G, const Phys &P, const float *wallT, float nu,
                           float ka, double *sums, cudaStream_t stream) {
     WallT W;
     for (int k = 0; k < 6; ++k) W.Tw[k] = wallT[k];
-    k_eps_sq<<<diag_blocks(G), kDiagThreads, 0, stream>>>(mom, G, P, W, nu, ka, sums);
+    k_eps_sq<<<resident_blocks(reinterpret_cast<const void *>(&k_eps_sq), 0, G.n), kDiagThreads, 0, stream>>>(
+        mom, G, P, W, nu, ka, sums);
     return cudaGetLastError();
 }
 
@@ -510,8 +531,8 @@ cudaError_t launch_eps_hist(const float *mom, const Geom &G, const Phys &P, cons
     WallT W;
     for (int k = 0; k < 6; ++k) W.Tw[k] = wallT[k];
     const size_t shmem = (size_t)2 * nbins * sizeof(unsigned int);
-    k_eps_hist<<<diag_blocks(G), kDiagThreads, shmem, stream>>>(mom, G, P, W, nu, ka, scale_u, scale_t, nbins,
-                                                               counts);
+    k_eps_hist<<<resident_blocks(reinterpret_cast<const void *>(&k_eps_hist), shmem, G.n), kDiagThreads, shmem,
+                 stream>>>(mom, G, P, W, nu, ka, scale_u, scale_t, nbins, counts);
     return cudaGetLastError();
 }
 
@@ -612,10 +633,13 @@ cudaError_t launch_nu_profile(const float *mom, const Geom &G, const Phys &P, co
     for (int k = 0; k < 6; ++k) W.Tw[k] = wallT[k];
     const int na = axis == 0 ? G.nx : axis == 1 ? G.ny : G.nz;
     if (na <= kProfileSharedMax)
-        k_nu_profile<true><<<diag_blocks(G), kDiagThreads, (size_t)na * sizeof(double), stream>>>(
-            mom, G, P, W, axis, H / kappa, H, prof);
+        k_nu_profile<true><<<resident_blocks(reinterpret_cast<const void *>(&k_nu_profile<true>),
+                                             (size_t)na * sizeof(double), G.n),
+                             kDiagThreads, (size_t)na * sizeof(double), stream>>>(mom, G, P, W, axis, H / kappa, H,
+                                                                                  prof);
     else
-        k_nu_profile<false><<<diag_blocks(G), kDiagThreads, 0, stream>>>(mom, G, P, W, axis, H / kappa, H, prof);
+        k_nu_profile<false><<<resident_blocks(reinterpret_cast<const void *>(&k_nu_profile<false>), 0, G.n),
+                              kDiagThreads, 0, stream>>>(mom, G, P, W, axis, H / kappa, H, prof);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_nu_midline<<<6, kDiagThreads, 0, stream>>>(mom, G, P, W, H, mid);
