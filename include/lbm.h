@@ -200,7 +200,8 @@ lbm_status lbm_set_fields(lbm_ctx *ctx, const double *rho, const double *u3, con
  * then writes the equilibrium populations f^eq(rho, u), g^eq(T, u)
  * (Sec. 2.2, 2.3) of the uploaded fields, as lbm_set_fields does, without
  * synchronising.  The step counter is kept; time averages are not touched.
- * LBM_ERR_STATE when no upload is pending (each upload is applied once). */
+ * LBM_ERR_STATE when no upload is pending (each upload is applied once); a
+ * second upload before lbm_apply_fields replaces the first. */
 lbm_status lbm_upload_fields(lbm_ctx *ctx, const double *rho, const double *u3, const double *T);
 lbm_status lbm_apply_fields(lbm_ctx *ctx);
 
